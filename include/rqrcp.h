@@ -1,0 +1,167 @@
+/*
+ * rqrcp.h -- C ABI of the GB300 (sm_103a) RQRCP / TRQRCP / TUXV library.
+ *
+ * Randomized QR with column pivoting and its truncated low-rank forms,
+ * after Duersch & Gu, "Randomized Projection for Rank-Revealing Matrix
+ * Factorizations and Low-Rank Approximations" (arXiv 2008.04447).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices are column-major with LAPACK leading dimensions (element (i, j)
+ *   of an m x n matrix X with leading dimension ldx is X[i + j*ldx],
+ *   ldx >= max(1, rows)).
+ * - Every matrix / vector pointer is a DEVICE pointer owned by the caller;
+ *   the library never frees or retains it beyond the call's stream work.
+ * - Element type follows `prec`: RQ_FP64 -> double, RQ_FP32 and RQ_MIXED ->
+ *   float (A, Omega, tau, R, Y, U, X, V, sigma).  Index vectors are int32.
+ * - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *   stream).  The return value reports argument / launch problems found on
+ *   the host; numerical status is written to the caller's device `info` word.
+ * - The library owns only its workspace, held in the handle (see
+ *   rq_workspace_size / rq_set_workspace).  No exception crosses the ABI.
+ *
+ * Return codes: RQ_OK (0); -i when argument i (1-based, counting the handle
+ * as argument 1) is invalid; or one of the named negative codes below.
+ */
+#ifndef RQRCP_H
+#define RQRCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RQ_OK 0
+#define RQ_ENOMEM (-1000)   /* workspace allocation failed / caller workspace too small */
+#define RQ_ECUDA (-1001)    /* a CUDA launch or runtime call failed (see rq_last_error) */
+#define RQ_ETIMEOUT (-1002) /* a bounded device-side wait ran out (kernel returned early) */
+#define RQ_ENOTIMPL (-1003) /* combination of arguments not supported by this build */
+#define RQ_EHANDLE (-1004)  /* NULL or destroyed handle */
+
+/* Arithmetic / storage precision of a call. */
+#define RQ_FP64 0  /* everything FP64 */
+#define RQ_FP32 1  /* FP32 storage and updates; Householder vectors, tau, norms in FP64 */
+#define RQ_MIXED 2 /* FP32 storage, BF16 sketch, FP32 updates; FP64 reflectors, norms, core SVD */
+
+/* Operations, for rq_workspace_size. */
+#define RQ_OP_RQRCP 0
+#define RQ_OP_TRQRCP 1
+#define RQ_OP_TUXV 2
+#define RQ_OP_QR 3
+
+typedef struct rq_handle_s* rq_handle;
+typedef void* rq_stream; /* cudaStream_t */
+
+/* Create a handle bound to the current CUDA device.  Ownership of *h passes
+ * to the caller, who releases it with rq_destroy. */
+int rq_create(rq_handle* h);
+
+/* Release the handle and any workspace the library allocated for it.  The
+ * caller must make sure no work that uses the handle is still running. */
+int rq_destroy(rq_handle h);
+
+/* Bytes of device workspace that operation `op` needs for these sizes. */
+int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b, int p,
+                      size_t* bytes);
+
+/* Give the handle a caller-owned device workspace (NULL / 0 to go back to
+ * library-managed workspace).  The caller keeps ownership and must keep it
+ * alive while work issued through the handle runs.  A call whose need exceeds
+ * a caller workspace returns RQ_ENOMEM.  Without a caller workspace the
+ * library grows its own with cudaMalloc (synchronising the device). */
+int rq_set_workspace(rq_handle h, void* dptr, size_t bytes);
+
+/* Copy the last host-side error message of this handle into buf. */
+int rq_last_error(rq_handle h, char* buf, size_t len);
+
+/* Number of this library's kernel launches issued through the handle so far. */
+long long rq_launch_count(rq_handle h);
+
+/* Phases of the factorisations, for per-phase timing. */
+#define RQ_PHASE_SKETCH 0        /* B = Omega A (Alg. 4 line "form the initial sample") */
+#define RQ_PHASE_SAMPLE_QRCP 1   /* block pivots from the sample (Sec. 3.2) */
+#define RQ_PHASE_PERMUTE 2       /* column permutation of A and jpvt */
+#define RQ_PHASE_PANEL 3         /* Householder panel + compact-WY T */
+#define RQ_PHASE_TRAILING 4      /* W^T = T^T Y^T A2, A2 -= Y W^T (block reflector) */
+#define RQ_PHASE_SAMPLE_UPDATE 5 /* Eq. (update1) */
+#define RQ_PHASE_OTHER 6         /* TRQRCP / TUXV products, small kernels */
+#define RQ_NUM_PHASES 7
+
+/* Enable (1) or disable (0) per-phase timing: CUDA events are recorded on the
+ * call's stream around each phase.  Adds two event records per phase. */
+int rq_profile_enable(rq_handle h, int enable);
+
+/* Synchronise on the recorded events and return, per phase (arrays of
+ * `nphases` entries, any may be NULL): elapsed milliseconds, algorithmic
+ * floating-point operations, algorithmic HBM bytes and kernel launches,
+ * summed since the last read.  Clears the accumulated records. */
+int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double* bytes,
+                    long long* launches);
+
+/*
+ * rq_rqrcp -- Randomized QR with column pivoting, Alg. 4 (Sec. 3.4), with the
+ * sample update formula Eq. (update1).
+ *
+ *   A      [in/out] m x n, lda >= m.  On exit: rows 0..k-1 on and above the
+ *          diagonal hold R (k x n upper trapezoidal, pivoted column order);
+ *          below the diagonal of columns 0..k-1 the Householder vectors v
+ *          (v_1 = 1 implicit, H = I - v tau v^T); the block A[k:m, k:n] holds
+ *          the trailing matrix (R22) left by the last block update.
+ *   b      block size (pivots per sample), 1 <= b.
+ *   p      oversampling; the sample has l = b + p rows, p >= 0.
+ *   k      factorisation rank, 1 <= k <= min(m, n).
+ *   Omega  l x m Gaussian compression matrix (ldo >= l), read only; the same
+ *          Omega serves every block through the update formula.
+ *   tau    k reflector coefficients (out).
+ *   jpvt   n int32 (out): 0-based column permutation, A_in[:, jpvt] = Q R.
+ *   info   device int32 (out): 0, or j > 0 when R(j-1, j-1) is exactly zero
+ *          (first such j; the factorisation still completes).
+ * Precisions: RQ_FP64 and RQ_FP32.
+ */
+int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
+             const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
+
+/*
+ * rq_qr -- unpivoted blocked Householder QR with the same panel and block
+ * reflector kernels as rq_rqrcp but no sampling or pivoting: the QR the paper
+ * compares RQRCP against ("identical to RQRCP after eliminating sample
+ * operations and pivoting", Sec. 5.2, Table 3).  A is overwritten as in
+ * rq_rqrcp with k = min(m, n); tau has min(m, n) entries.
+ */
+int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* tau, int* info,
+          rq_stream stream);
+
+/*
+ * rq_trqrcp -- truncated RQRCP without trailing update, Alg. 5 (Sec. 4.1),
+ * through the accumulated inner products W^T = T^T Y^T A.
+ *   A   m x n, READ ONLY.
+ *   Y   m x k (ldy >= m, out): reflectors, unit diagonal, zeros above.
+ *   tau k (out).
+ *   R   k x n (ldr >= k, out): upper trapezoidal, pivoted column order.
+ *   jpvt, info as for rq_rqrcp.
+ */
+int rq_trqrcp(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k,
+              const void* Omega, int ldo, void* Y, int ldy, void* tau, void* R, int ldr, int* jpvt,
+              int* info, rq_stream stream);
+
+/*
+ * rq_tuxv -- TUXV approximation of the truncated SVD, Alg. 6 with j_max = 1
+ * (Sec. 4.2, Eq. TUXV): A ~= U X V^T.
+ *   U     m x k (ldu >= m, out), orthonormal columns.
+ *   X     k x k (ldx >= k, out), upper triangular; diag(sigma) when sigma != NULL.
+ *   V     n x k (ldv >= n, out), orthonormal columns.
+ *   sigma NULL, or k entries (out): the singular values of X from a one-sided
+ *         Jacobi SVD (descending); U and V are then rotated by the core
+ *         singular vectors and X is returned as diag(sigma).
+ */
+int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k,
+            const void* Omega, int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv,
+            void* sigma, int* info, rq_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQRCP_H */

@@ -1,0 +1,157 @@
+"""ctypes binding of librqrcp.so (include/rqrcp.h): argument marshalling only.
+
+Every exported C function is re-exported here under the same name.  Matrix
+arguments may be passed as raw device addresses (int) or as CUDA tensors; a
+tensor is passed by its data pointer.  Column-major matrices are tensors of
+shape (rows, cols) with stride (1, ld) -- e.g. ``x.t().contiguous().t()``.
+
+There is no fallback: if the library is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librqrcp.so")
+
+RQ_OK = 0
+RQ_ENOMEM = -1000
+RQ_ECUDA = -1001
+RQ_ETIMEOUT = -1002
+RQ_ENOTIMPL = -1003
+RQ_EHANDLE = -1004
+
+RQ_FP64, RQ_FP32, RQ_MIXED = 0, 1, 2
+RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR = 0, 1, 2, 3
+PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing", "sample_update", "other"]
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "rq_create": ([ctypes.POINTER(_P)], _I),
+    "rq_destroy": ([_P], _I),
+    "rq_workspace_size": ([_P, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)], _I),
+    "rq_set_workspace": ([_P, _P, ctypes.c_size_t], _I),
+    "rq_last_error": ([_P, ctypes.c_char_p, ctypes.c_size_t], _I),
+    "rq_launch_count": ([_P], ctypes.c_longlong),
+    "rq_profile_enable": ([_P, _I], _I),
+    "rq_profile_read": ([_P, _I, _P, _P, _P, _P], _I),
+    "rq_rqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P], _I),
+    "rq_qr": ([_P, _I, _I, _I, _P, _I, _I, _P, _P, _P], _I),
+    "rq_trqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _P, _P], _I),
+    "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librqrcp.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librqrcp.so not built ({path}); run paper_2008_04447_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("device tensor expected")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def rq_create():
+    h = _P()
+    rc = load().rq_create(ctypes.byref(h))
+    if rc != RQ_OK:
+        raise RuntimeError(f"rq_create failed: {rc}")
+    return h
+
+
+def rq_destroy(h):
+    return load().rq_destroy(h)
+
+
+def rq_workspace_size(h, op, prec, m, n, k, b, p):
+    out = ctypes.c_size_t()
+    rc = load().rq_workspace_size(h, op, prec, m, n, k, b, p, ctypes.byref(out))
+    return rc, out.value
+
+
+def rq_set_workspace(h, dptr, nbytes):
+    return load().rq_set_workspace(h, _ptr(dptr), nbytes)
+
+
+def rq_last_error(h):
+    buf = ctypes.create_string_buffer(256)
+    load().rq_last_error(h, buf, 256)
+    return buf.value.decode()
+
+
+def rq_launch_count(h):
+    return int(load().rq_launch_count(h))
+
+
+def rq_profile_enable(h, enable):
+    return load().rq_profile_enable(h, 1 if enable else 0)
+
+
+def rq_profile_read(h):
+    """Per-phase {name: (ms, flops, bytes, launches)} since the last read (synchronises)."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    fl = (ctypes.c_double * n)()
+    by = (ctypes.c_double * n)()
+    la = (ctypes.c_longlong * n)()
+    rc = load().rq_profile_read(h, n, ctypes.cast(ms, _P), ctypes.cast(fl, _P), ctypes.cast(by, _P),
+                                ctypes.cast(la, _P))
+    if rc != RQ_OK:
+        raise RuntimeError(f"rq_profile_read failed: {rc}")
+    return {PHASES[i]: (ms[i], fl[i], by[i], la[i]) for i in range(n)}
+
+
+def rq_rqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
+    return load().rq_rqrcp(h, prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
+                           _ptr(info), _stream(stream))
+
+
+def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):
+    return load().rq_qr(h, prec, m, n, _ptr(A), lda, b, _ptr(tau), _ptr(info), _stream(stream))
+
+
+def rq_trqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, Y, ldy, tau, R, ldr, jpvt, info, stream=None):
+    return load().rq_trqrcp(h, prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(Y), ldy, _ptr(tau),
+                            _ptr(R), ldr, _ptr(jpvt), _ptr(info), _stream(stream))
+
+
+def rq_tuxv(h, prec, m, n, A, lda, b, p, k, Omega, ldo, U, ldu, X, ldx, V, ldv, sigma, info, stream=None):
+    return load().rq_tuxv(h, prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(U), ldu, _ptr(X), ldx,
+                          _ptr(V), ldv, _ptr(sigma), _ptr(info), _stream(stream))

@@ -1,0 +1,262 @@
+// Partial QRCP of the sample matrix B (Sec. 3.2; Alg. 4, "get b column pivots").
+//
+// One cooperative launch per block of pivots.  Each CTA holds a slab of the
+// sample's columns in shared memory (FP64, row-major inside the slab so that
+// consecutive threads touch consecutive columns) for all `steps` decisions,
+// so B is read from HBM once and written once per block.  Per decision:
+//   1. every CTA finds its best alive column (max downdated squared norm,
+//      ties -> lowest current position) and publishes (norm^2, position,
+//      column values) to a double-buffered candidate table;
+//   2. one grid barrier;
+//   3. every CTA reduces the table in the same order (so all agree bit for
+//      bit), rebuilds the Householder vector of the winner in FP64, applies it
+//      to its alive columns and downdates their norms (removing the
+//      contribution of the finished row, Alg. 1), recomputing a norm from
+//      the remaining rows when the downdated value has fallen to sqrt(eps)
+//      of its last exactly computed value.
+// Column exchanges are never moved in memory: each CTA tracks the current
+// position of its columns (only the column at position i moves per swap), so
+// ties resolve exactly as with physical swaps.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rq {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxSteps = 256;
+
+template <typename TS>
+struct SqArgs {
+  const TS* B;
+  int ldb, l, nt, steps;
+  TS* Bn;
+  int ldbn;
+  double* S11;
+  int lds;
+  int* swaps;
+  int* src;
+  int* chg;      // 2*steps: positions whose column changes (-1 = none)
+  double* cand;  // 2 * G * (l + 2)
+  unsigned int* bar;
+  int* err;
+  int cpc;  // columns per CTA
+};
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
+  extern __shared__ double sm[];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int l = a.l, cpc = a.cpc, steps = a.steps;
+  const int c0 = cta * cpc;
+  const int nc = max(0, min(cpc, a.nt - c0));
+  const double tol = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
+  double* s = sm;                             // s[r * cpc + c]
+  double* nu2 = s + (size_t)l * cpc;
+  double* ref2 = nu2 + cpc;
+  double* vv = ref2 + cpc;  // l
+  int* pos = reinterpret_cast<int*>(vv + l);
+  int* alive = pos + cpc;
+  __shared__ double red_v[kWarps];
+  __shared__ int red_p[kWarps], red_t[kWarps];
+  __shared__ int s_best_lc, s_win_cta, s_win_pos;
+  __shared__ double s_tau;
+  __shared__ int s_swaps[kMaxSteps];
+  const int rec = l + 2;
+
+  for (int e = tid; e < l * nc; e += kThreads) {
+    const int r = e % l, c = e / l;
+    s[(size_t)r * cpc + c] = static_cast<double>(a.B[(size_t)(c0 + c) * a.ldb + r]);
+  }
+  __syncthreads();
+  for (int c = tid; c < nc; c += kThreads) {
+    double acc = 0.0;
+    for (int r = 0; r < l; ++r) {
+      const double x = s[(size_t)r * cpc + c];
+      acc = fma(x, x, acc);
+    }
+    nu2[c] = acc;
+    ref2[c] = acc;
+    pos[c] = c0 + c;
+    alive[c] = 1;
+  }
+  __syncthreads();
+
+  for (int i = 0; i < steps; ++i) {
+    const int par = i & 1;
+    double* tab = a.cand + (size_t)par * G * rec;
+    // (1) local best alive column
+    double bv = -1.0;
+    int bp = -1, bt = -1;
+    for (int c = tid; c < nc; c += kThreads)
+      if (alive[c] && better(nu2[c], pos[c], bv, bp)) { bv = nu2[c]; bp = pos[c]; bt = c; }
+    warp_argmax(bv, bp, bt);
+    if (lane == 0) { red_v[warp] = bv; red_p[warp] = bp; red_t[warp] = bt; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < kWarps ? red_v[lane] : -1.0;
+      bp = lane < kWarps ? red_p[lane] : -1;
+      bt = lane < kWarps ? red_t[lane] : -1;
+      warp_argmax(bv, bp, bt);
+      if (lane == 0) {
+        s_best_lc = bt;
+        tab[(size_t)cta * rec + 0] = bv;
+        tab[(size_t)cta * rec + 1] = static_cast<double>(bp);
+      }
+    }
+    __syncthreads();
+    {
+      const int lc = s_best_lc;
+      if (lc >= 0)
+        for (int r = tid; r < l; r += kThreads) tab[(size_t)cta * rec + 2 + r] = s[(size_t)r * cpc + lc];
+    }
+    // (2)
+    if (!grid_barrier(a.bar, G, a.err)) return;
+    // (3) global winner: same reduction order on every CTA
+    if (warp == 0) {
+      double gv = -1.0;
+      int gp = -1, gt = -1;
+      for (int q = lane; q < G; q += 32) {
+        const double v = __ldcg(tab + (size_t)q * rec + 0);
+        const int p = static_cast<int>(__ldcg(tab + (size_t)q * rec + 1));
+        if (better(v, p, gv, gp)) { gv = v; gp = p; gt = q; }
+      }
+      warp_argmax(gv, gp, gt);
+      if (lane == 0) { s_win_cta = gt; s_win_pos = gp; }
+    }
+    __syncthreads();
+    const int wc = s_win_cta, q = s_win_pos;
+    for (int r = tid; r < l; r += kThreads) vv[r] = __ldcg(tab + (size_t)wc * rec + 2 + r);
+    if (tid == 0) {
+      if (wc == cta) { alive[s_best_lc] = 0; pos[s_best_lc] = i; }
+      if (cta == 0) { a.swaps[i] = q; s_swaps[i] = q; }
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += kThreads)
+      if (alive[c] && pos[c] == i) pos[c] = q;
+    // reflector of the winner, rows i..l-1 (Sec. 2 formula, v_i = 1)
+    if (warp == 0) {
+      double x2 = 0.0;
+      for (int r = i + 1 + lane; r < l; r += 32) x2 = fma(vv[r], vv[r], x2);
+      x2 = warp_sum(x2);
+      const double alpha = vv[i];
+      const double nrm2 = fma(alpha, alpha, x2);
+      double beta = 0.0, y1 = 1.0;
+      const bool zero = !(nrm2 > 0.0);
+      if (!zero) {
+        const double nrm = sqrt(nrm2);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        y1 = alpha - beta;
+      }
+      if (cta == 0) {
+        double* col = a.S11 + (size_t)i * a.lds;
+        for (int r = lane; r < steps; r += 32) col[r] = r < i ? vv[r] : (r == i ? beta : 0.0);
+      }
+      __syncwarp();
+      double v2 = 0.0;
+      for (int r = lane; r < l; r += 32) {
+        double v;
+        if (r < i) v = 0.0;
+        else if (r == i) v = 1.0;
+        else v = zero ? 0.0 : vv[r] / y1;
+        vv[r] = v;
+        if (r > i) v2 = fma(v, v, v2);
+      }
+      v2 = warp_sum(v2);
+      if (lane == 0) s_tau = zero ? 0.0 : 2.0 / (1.0 + v2);
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    for (int c = tid; c < nc; c += kThreads) {
+      if (!alive[c]) continue;
+      if (tau != 0.0) {
+        double w = s[(size_t)i * cpc + c];
+        for (int r = i + 1; r < l; ++r) w = fma(vv[r], s[(size_t)r * cpc + c], w);
+        const double tw = tau * w;
+        s[(size_t)i * cpc + c] -= tw;
+        for (int r = i + 1; r < l; ++r) s[(size_t)r * cpc + c] = fma(-tw, vv[r], s[(size_t)r * cpc + c]);
+      }
+      const double x = s[(size_t)i * cpc + c];
+      double nn = nu2[c] - x * x;
+      if (nn <= tol * ref2[c]) {
+        nn = 0.0;
+        for (int r = i + 1; r < l; ++r) {
+          const double y = s[(size_t)r * cpc + c];
+          nn = fma(y, y, nn);
+        }
+        ref2[c] = nn;
+      }
+      nu2[c] = nn;
+    }
+    __syncthreads();
+  }
+
+  // outputs: new order of the columns, the reordered trailing sample
+  for (int c = tid; c < nc; c += kThreads) a.src[pos[c]] = c0 + c;
+  for (int e = tid; e < l * nc; e += kThreads) {
+    const int r = e % l, c = e / l;
+    if (alive[c]) a.Bn[(size_t)(pos[c] - steps) * a.ldbn + r] = static_cast<TS>(s[(size_t)r * cpc + c]);
+  }
+  if (cta == 0) {
+    for (int i = tid; i < steps; i += kThreads) {
+      a.chg[i] = i;
+      const int qq = s_swaps[i];
+      bool keep = qq >= steps;
+      for (int j = 0; j < i && keep; ++j) keep = s_swaps[j] != qq;
+      a.chg[steps + i] = keep ? qq : -1;
+    }
+  }
+}
+
+template <typename TS>
+size_t smem_bytes(int l, int cpc) {
+  return ((size_t)l * cpc + 2 * (size_t)cpc + l) * sizeof(double) + 2 * (size_t)cpc * sizeof(int);
+}
+
+}  // namespace
+
+size_t sample_qrcp_scratch_doubles(int l, int num_sms) { return 2 * (size_t)num_sms * (l + 2); }
+
+template <typename TS>
+cudaError_t sample_qrcp(const Ctx& c, const TS* B, int ldb, int l, int nt, int steps, TS* Bn,
+                        int ldbn, double* S11, int lds, int* swaps, int* src, int* chg,
+                        double* cand) {
+  if (steps > kMaxSteps || steps > nt || steps > l) return cudaErrorInvalidValue;
+  int G = (nt + 31) / 32;
+  if (G > c.num_sms) G = c.num_sms;
+  if (G < 1) G = 1;
+  int cpc = (nt + G - 1) / G;
+  size_t smem = smem_bytes<TS>(l, cpc);
+  static int max_optin = -1;
+  if (max_optin < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  if (smem > (size_t)max_optin - 2048) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(sample_qrcp_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_qrcp_kernel<TS>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm * c.num_sms < G) return cudaErrorCooperativeLaunchTooLarge;
+  SqArgs<TS> a{B, ldb, l, nt, steps, Bn, ldbn, S11, lds, swaps, src, chg, cand, c.bar, c.err, cpc};
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void*)sample_qrcp_kernel<TS>, dim3(G), dim3(kThreads), args, smem,
+                                  c.stream);
+  ++*c.launches;
+  return e;
+}
+
+template cudaError_t sample_qrcp<double>(const Ctx&, const double*, int, int, int, int, double*, int,
+                                         double*, int, int*, int*, int*, double*);
+template cudaError_t sample_qrcp<float>(const Ctx&, const float*, int, int, int, int, float*, int,
+                                        double*, int, int*, int*, int*, double*);
+
+}  // namespace rq

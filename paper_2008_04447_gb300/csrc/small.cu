@@ -1,0 +1,179 @@
+// Small kernels of the RQRCP path: column permutation, the sample update
+// (Eq. update1), index initialisation, the LAPACK-style info word.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rq {
+namespace {
+
+// Gather the changed columns (new position e <- old position src[e]) to tmp.
+template <typename TS>
+__global__ void perm_gather(const TS* __restrict__ A, int lda, int m, const int* __restrict__ chg,
+                            const int* __restrict__ src, const int* __restrict__ jpvt, TS* __restrict__ tmp,
+                            int* __restrict__ jtmp) {
+  const int slot = blockIdx.y;
+  const int e = chg[slot];
+  if (e < 0) return;
+  const int s = src[e];
+  const TS* col = A + (size_t)s * lda;
+  TS* out = tmp + (size_t)slot * m;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) out[r] = col[r];
+  if (blockIdx.x == 0 && threadIdx.x == 0) jtmp[slot] = jpvt[s];
+}
+
+template <typename TS>
+__global__ void perm_scatter(TS* __restrict__ A, int lda, int m, const int* __restrict__ chg,
+                             const TS* __restrict__ tmp, const int* __restrict__ jtmp, int* __restrict__ jpvt) {
+  const int slot = blockIdx.y;
+  const int e = chg[slot];
+  if (e < 0) return;
+  TS* col = A + (size_t)e * lda;
+  const TS* in = tmp + (size_t)slot * m;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) col[r] = in[r];
+  if (blockIdx.x == 0 && threadIdx.x == 0) jpvt[e] = jtmp[slot];
+}
+
+// Omegahat11 = S11 R11^{-1}: row r solves x R11 = S11(r, :) (both upper
+// triangular, so x(r, j) = 0 for j < r).  One thread per row, R11 in shared memory.
+template <typename TS>
+__global__ void omegahat_kernel(const double* __restrict__ S11, int lds, const TS* __restrict__ R11, int ldr,
+                                int bj, double* __restrict__ Oh, int ldo) {
+  extern __shared__ double sR[];  // bj x bj, column-major
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) {
+    const int i = e % bj, j = e / bj;
+    sR[e] = i <= j ? static_cast<double>(R11[i + (size_t)j * ldr]) : 0.0;
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= bj) return;
+  double* x = Oh + r;  // row r of Oh, stride ldo
+  for (int j = 0; j < r; ++j) x[(size_t)j * ldo] = 0.0;
+  for (int j = r; j < bj; ++j) {
+    double acc = S11[r + (size_t)j * lds];
+    for (int i = r; i < j; ++i) acc = fma(-x[(size_t)i * ldo], sR[i + j * bj], acc);
+    const double d = sR[j + j * bj];
+    x[(size_t)j * ldo] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+// B1 -= Oh * R12 (K = bj), one thread per output entry, FP64 accumulation.
+template <typename TS>
+__global__ void sample_update_kernel(int bj, int n2, const double* __restrict__ Oh, int ldo,
+                                     const TS* __restrict__ R12, int ldr, TS* __restrict__ B1, int ldb) {
+  extern __shared__ double sO[];  // bj x bj
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) sO[e] = Oh[(e % bj) + (size_t)(e / bj) * ldo];
+  __syncthreads();
+  const int col = blockIdx.x;
+  if (col >= n2) return;
+  const TS* rc = R12 + (size_t)col * ldr;
+  TS* bc = B1 + (size_t)col * ldb;
+  for (int r = threadIdx.x; r < bj; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], static_cast<double>(rc[i]), acc);
+    bc[r] = static_cast<TS>(static_cast<double>(bc[r]) - acc);
+  }
+}
+
+__global__ void iota_kernel(int* v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
+// info = first j (1-based) with A(j-1, j-1) == 0, or RQ_ETIMEOUT if a bounded
+// wait gave up somewhere in the call.
+template <typename TS>
+__global__ void info_kernel(const TS* __restrict__ A, int lda, int k, const int* __restrict__ err,
+                            int* __restrict__ info) {
+  __shared__ int first;
+  if (threadIdx.x == 0) first = k;
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    if (A[(size_t)i * lda + i] == TS(0)) atomicMin(&first, i);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int e = *reinterpret_cast<const volatile int*>(err);
+    *info = e != 0 ? e : (first < k ? first + 1 : 0);
+  }
+}
+
+template <typename TD, typename TS>
+__global__ void convert_kernel(int rows, int cols, const TS* __restrict__ s, int lds, TD* __restrict__ d, int ldd) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = e % rows, j = e / rows;
+    d[i + (size_t)j * ldd] = static_cast<TD>(s[i + (size_t)j * lds]);
+  }
+}
+
+}  // namespace
+
+template <typename TS>
+cudaError_t permute_columns(const Ctx& c, TS* A, int lda, int m, int steps, const int* chg, const int* src,
+                            int* jpvt, TS* tmp, int* jtmp) {
+  if (steps <= 0) return cudaSuccess;
+  int bx = (m + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, 2 * steps);
+  perm_gather<TS><<<grid, 256, 0, c.stream>>>(A, lda, m, chg, src, jpvt, tmp, jtmp);
+  perm_scatter<TS><<<grid, 256, 0, c.stream>>>(A, lda, m, chg, tmp, jtmp, jpvt);
+  *c.launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t omegahat11(const Ctx& c, const double* S11, int lds, const TS* R11, int ldr, int bj, double* Oh,
+                       int ldo) {
+  const int threads = bj <= 32 ? 32 : (bj <= 64 ? 64 : (bj <= 128 ? 128 : 256));
+  omegahat_kernel<TS><<<(bj + threads - 1) / threads, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(
+      S11, lds, R11, ldr, bj, Oh, ldo);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t sample_update(const Ctx& c, int bj, int n2, const double* Oh, int ldo, const TS* R12, int ldr,
+                          TS* B1, int ldb) {
+  if (n2 <= 0) return cudaSuccess;
+  const int threads = bj <= 32 ? 32 : (bj <= 64 ? 64 : (bj <= 128 ? 128 : 256));
+  sample_update_kernel<TS><<<n2, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(bj, n2, Oh, ldo, R12,
+                                                                                         ldr, B1, ldb);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t iota(const Ctx& c, int* v, int n) {
+  iota_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, c.stream>>>(v, n);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t finish_info(const Ctx& c, const TS* A, int lda, int k, int* info) {
+  info_kernel<TS><<<1, 256, 0, c.stream>>>(A, lda, k, c.err, info);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+template <typename TD, typename TS>
+cudaError_t convert(const Ctx& c, int rows, int cols, const TS* src, int lds, TD* dst, int ldd) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  size_t total = (size_t)rows * cols;
+  int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  convert_kernel<TD, TS><<<blocks, 256, 0, c.stream>>>(rows, cols, src, lds, dst, ldd);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+#define RQ_INST(TS)                                                                                          \
+  template cudaError_t permute_columns<TS>(const Ctx&, TS*, int, int, int, const int*, const int*, int*, TS*, \
+                                           int*);                                                            \
+  template cudaError_t omegahat11<TS>(const Ctx&, const double*, int, const TS*, int, int, double*, int);    \
+  template cudaError_t sample_update<TS>(const Ctx&, int, int, const double*, int, const TS*, int, TS*, int); \
+  template cudaError_t finish_info<TS>(const Ctx&, const TS*, int, int, int*);
+RQ_INST(double)
+RQ_INST(float)
+template cudaError_t convert<float, double>(const Ctx&, int, int, const double*, int, float*, int);
+template cudaError_t convert<double, float>(const Ctx&, int, int, const float*, int, double*, int);
+template cudaError_t convert<float, float>(const Ctx&, int, int, const float*, int, float*, int);
+template cudaError_t convert<double, double>(const Ctx&, int, int, const double*, int, double*, int);
+
+}  // namespace rq

@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads and exports every symbol include/rqrcp.h declares.
+
+No compute call is made (no GPU needed); argument validation paths that return
+before touching the device are exercised where they need no handle.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|long long|size_t|void)\s+(rq_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_04447_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ("rq_create", "rq_destroy", "rq_workspace_size", "rq_rqrcp", "rq_qr", "rq_trqrcp", "rq_tuxv"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in sorted(_declared()):
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    from paper_2008_04447_gb300 import _lib
+    assert set(_lib.exported_symbols()) == _declared()
+
+
+def test_null_handle_is_rejected(lib):
+    from paper_2008_04447_gb300 import _lib
+    L = _lib.load()
+    assert L.rq_destroy(None) == _lib.RQ_EHANDLE
+    assert L.rq_rqrcp(None, 0, 1, 1, None, 1, 1, 0, 1, None, 1, None, None, None, None) == _lib.RQ_EHANDLE
+    assert L.rq_launch_count(None) == -1
