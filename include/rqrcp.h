@@ -39,6 +39,7 @@ extern "C" {
 #define RQ_ETIMEOUT (-1002) /* a bounded device-side wait ran out (kernel returned early) */
 #define RQ_ENOTIMPL (-1003) /* combination of arguments not supported by this build */
 #define RQ_EHANDLE (-1004)  /* NULL or destroyed handle */
+#define RQ_ETOOBIG (-1005)  /* rq_rqrcp_noalloc: the problem needs more scratch than the fixed array */
 
 /* Arithmetic / storage precision of a call. */
 #define RQ_FP64 0  /* everything FP64 */
@@ -122,6 +123,28 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  */
 int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
              const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
+
+/*
+ * rq_rqrcp_noalloc -- the same factorisation as rq_rqrcp (same arguments
+ * without the handle, same outputs), for callers that cannot allocate device
+ * memory when they call: a process whose device memory is all owned by
+ * another allocator, or a latency-bound service that cannot afford the
+ * device-wide synchronisation of cudaMalloc / cudaFree mid-request.  The
+ * paper has no counterpart; this is a deployment variant.
+ *
+ * It allocates nothing: its scratch is a fixed device array of
+ * RQ_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  A problem whose scratch
+ * (about 8 B x (2 l n + 5 m b + b n + 3 b^2) for FP64, half the matrix terms
+ * for FP32) exceeds it returns RQ_ETOOBIG before any launch.  All calls share
+ * the array, so calls that overlap on the GPU race: serialise them.  The
+ * first call on each device looks up the array's address with that device
+ * current; make it before any stream capture.  prec is RQ_FP64 or RQ_FP32;
+ * argument errors return -(index), counting prec as argument 1.
+ */
+#define RQ_NOALLOC_SCRATCH_BYTES (16u << 20)
+int rq_rqrcp_noalloc(int prec, int m, int n, void* A, int lda, int b, int p, int k, const void* Omega,
+                     int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
 
 /*
  * rq_qr -- unpivoted blocked Householder QR with the same panel and block

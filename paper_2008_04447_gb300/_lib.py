@@ -22,6 +22,8 @@ RQ_ECUDA = -1001
 RQ_ETIMEOUT = -1002
 RQ_ENOTIMPL = -1003
 RQ_EHANDLE = -1004
+RQ_ETOOBIG = -1005
+RQ_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 RQ_FP64, RQ_FP32, RQ_MIXED = 0, 1, 2
 RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR = 0, 1, 2, 3
@@ -39,6 +41,7 @@ _SIGS = {
     "rq_profile_enable": ([_P, _I], _I),
     "rq_profile_read": ([_P, _I, _P, _P, _P, _P], _I),
     "rq_rqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P], _I),
+    "rq_rqrcp_noalloc": ([_I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P], _I),
     "rq_qr": ([_P, _I, _I, _I, _P, _I, _I, _P, _P, _P], _I),
     "rq_trqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _P, _P], _I),
     "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
@@ -141,6 +144,11 @@ def rq_profile_read(h):
 def rq_rqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
     return load().rq_rqrcp(h, prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
                            _ptr(info), _stream(stream))
+
+
+def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
+    return load().rq_rqrcp_noalloc(prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
+                                   _ptr(info), _stream(stream))
 
 
 def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):
