@@ -183,6 +183,42 @@ int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, 
             const void* Omega, int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv,
             void* sigma, int* info, rq_stream stream);
 
+/*
+ * One problem of a batched TUXV call.  All pointers are device pointers owned
+ * by the caller; sizes and leading dimensions as for rq_tuxv.  Layout: twelve
+ * int32 then seven 64-bit pointers (104 bytes).
+ */
+typedef struct rq_problem {
+  int m, n, k, b, p;          /* 1 <= k <= min(m, n); 1 <= b <= 64; b + p <= 128 */
+  int lda, ldo, ldu, ldx, ldv;
+  int reserved0, reserved1;   /* set to 0 */
+  const void* A;              /* m x n, read only */
+  const void* Omega;          /* (b + p) x m */
+  void* U;                    /* m x k (out) */
+  void* X;                    /* k x k (out), upper triangular */
+  void* V;                    /* n x k (out) */
+  void* sigma;                /* must be NULL: the core SVD is not part of the batched path */
+  int* info;                  /* 1 int32 (out): 0, or RQ_ENOTIMPL when sigma was set */
+} rq_problem;
+
+/*
+ * rq_tuxv_batched -- TUXV (Alg. 6, j_max = 1, on truncated RQRCP, Alg. 5) of
+ * `count` independent problems of different sizes in one persistent kernel
+ * launch: each CTA takes the next problem from a device queue, so uneven
+ * problems balance on their own; list the largest problems first.
+ *   problems  device array of `count` rq_problem descriptors.
+ *   max_*     upper bounds of m, n, k, b, p over the batch (they size the
+ *             per-CTA scratch slots; a problem beyond them is undefined).
+ *   prec      RQ_FP32 (FP32 sketch) or RQ_MIXED (sketch inputs rounded to
+ *             BF16, FP32 accumulation); contractions FP32, Householder scalars,
+ *             sample norms, T and the Omegahat_11 solve FP64.
+ * The call issues one memset and one kernel; it does not synchronise, so it
+ * can be captured in a CUDA graph once the handle's workspace is large enough
+ * (make one call, or rq_set_workspace, before capturing).
+ */
+int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,
+                    int max_b, int max_p, rq_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,7 +41,7 @@ __all__ = [
     "reflector", "apply_reflector", "qr_householder", "form_q", "larft", "qrcp",
     "sample_qrcp", "SampleQRCP", "rqrcp", "RQRCPResult", "trqrcp", "TRQRCPResult",
     "tuxv", "TUXVResult", "jacobi_svd", "unpack_rqrcp", "qr_unpivoted", "reflectors_of",
-    "sample_update",
+    "sample_update", "round_bf16", "sketch",
 ]
 
 
@@ -357,7 +357,24 @@ class TRQRCPResult:
     info: int = 0
 
 
-def trqrcp(A, Omega, b, k):
+def round_bf16(x):
+    """Round to the nearest bfloat16 (ties to even), via float32; returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
+def sketch(Omega, A, inputs=None):
+    """The sample B = Omega A (Alg. 4); inputs="bf16" first rounds Omega and A to
+    bfloat16, the precision a reduced-precision sketch multiplies in, so that the
+    pivot decisions taken from B are taken in the same precision as there."""
+    if inputs == "bf16":
+        return round_bf16(Omega) @ round_bf16(A)
+    return Omega @ A
+
+
+def trqrcp(A, Omega, b, k, sketch_inputs=None):
     """Alg. 5: RQRCP without the trailing update, through W^T = T^T Y^T A (Sec. 4.1)."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -369,7 +386,7 @@ def trqrcp(A, Omega, b, k):
     R = np.zeros((k, n))
     tau = np.zeros(k)
     gaps = []
-    B = Omega @ Ap
+    B = sketch(Omega, Ap, sketch_inputs)
     for j0 in range(0, k, b):
         bj = min(b, k - j0)
         sq = sample_qrcp(B, bj)
@@ -477,11 +494,11 @@ def _fix_signs(U, V):
     return U * s, V * s
 
 
-def tuxv(A, Omega, b, k, jmax=1, svd=False):
+def tuxv(A, Omega, b, k, jmax=1, svd=False, sketch_inputs=None):
     """Alg. 6: A ~= U X V^T with TRQRCP, an LQ of R P^T and a QR of A V_1."""
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
-    tr = trqrcp(A, Omega, b, k)
+    tr = trqrcp(A, Omega, b, k, sketch_inputs=sketch_inputs)
     Z = np.zeros((k, n))
     Z[:, tr.jpvt] = tr.R                     # Z^(0) = R^(0) P^(0)T
     V, Xt = _qr_explicit(Z.T)                # LQ of Z^(0) through QR of its transpose

@@ -13,7 +13,8 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_OP_TRQRCP,  # noqa: F401
                    RQ_OP_TUXV, rq_create, rq_destroy, rq_last_error, rq_launch_count, rq_profile_enable,
-                   rq_profile_read, rq_qr, rq_rqrcp, rq_set_workspace, rq_trqrcp, rq_tuxv, rq_workspace_size)
+                   rq_profile_read, rq_qr, rq_rqrcp, rq_set_workspace, rq_trqrcp, rq_tuxv, rq_tuxv_batched,
+                   rq_workspace_size)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
 
@@ -85,6 +86,68 @@ class Handle:
         rc = rq_rqrcp(self.h, prec, m, n, A, _ld(A), b, p, k, Omega, _ld(Omega), tau, jpvt, info, stream)
         self._check(rc, "rq_rqrcp")
         return tau, jpvt, info
+
+    def trqrcp(self, A, Omega, b, p, k, prec=None, stream=None):
+        """Truncated RQRCP (Alg. 5); A is read only.  Returns (Y, tau, R, jpvt, info)."""
+        import torch
+        m, n = A.shape
+        prec = _prec_of(A) if prec is None else prec
+        Y = torch.empty((k, m), dtype=A.dtype, device=A.device).t()
+        R = torch.empty((n, k), dtype=A.dtype, device=A.device).t()
+        tau = torch.empty(k, dtype=A.dtype, device=A.device)
+        jpvt = torch.empty(n, dtype=torch.int32, device=A.device)
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+        rc = rq_trqrcp(self.h, prec, m, n, A, _ld(A), b, p, k, Omega, _ld(Omega), Y, m, tau, R, k, jpvt, info,
+                       stream)
+        self._check(rc, "rq_trqrcp")
+        return Y, tau, R, jpvt, info
+
+    def tuxv(self, A, Omega, b, p, k, svd=False, prec=None, stream=None):
+        """TUXV (Alg. 6, j_max = 1): A ~= U X V^T.  Returns (U, X, V, sigma or None, info)."""
+        import torch
+        m, n = A.shape
+        prec = _prec_of(A) if prec is None else prec
+        U = torch.empty((k, m), dtype=A.dtype, device=A.device).t()
+        X = torch.empty((k, k), dtype=A.dtype, device=A.device).t()
+        V = torch.empty((k, n), dtype=A.dtype, device=A.device).t()
+        sigma = torch.empty(k, dtype=A.dtype, device=A.device) if svd else None
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+        rc = rq_tuxv(self.h, prec, m, n, A, _ld(A), b, p, k, Omega, _ld(Omega), U, m, X, k, V, n, sigma, info, stream)
+        self._check(rc, "rq_tuxv")
+        return U, X, V, sigma, info
+
+    def tuxv_batched(self, problems, prec=RQ_MIXED, stream=None, outputs=None):
+        """Batched TUXV of [(A, Omega, b, p, k), ...] (column-major FP32 device tensors).
+
+        One persistent launch; returns [(U, X, V), ...] and the info tensor.
+        The descriptors are built on the host and copied to the device.
+        """
+        import numpy as np
+        import torch
+        dev = problems[0][0].device
+        if outputs is None:
+            outputs = []
+            for A, Om, b, p, k in problems:
+                m, n = A.shape
+                outputs.append((torch.empty((k, m), dtype=A.dtype, device=dev).t(),
+                                torch.empty((k, k), dtype=A.dtype, device=dev).t(),
+                                torch.empty((k, n), dtype=A.dtype, device=dev).t()))
+        info = torch.zeros(len(problems), dtype=torch.int32, device=dev)
+        desc = np.zeros(len(problems), dtype=_lib.problem_dtype())
+        for i, ((A, Om, b, p, k), (U, X, V)) in enumerate(zip(problems, outputs)):
+            m, n = A.shape
+            desc[i] = (m, n, k, b, p, _ld(A), _ld(Om), _ld(U), _ld(X), _ld(V), 0, 0, A.data_ptr(), Om.data_ptr(),
+                       U.data_ptr(), X.data_ptr(), V.data_ptr(), 0, info.data_ptr() + 4 * i)
+        d = torch.from_numpy(desc.view(np.uint8)).to(dev)
+        mm = max(int(A.shape[0]) for A, *_ in problems)
+        mn = max(int(A.shape[1]) for A, *_ in problems)
+        mk = max(int(t[4]) for t in problems)
+        mb = max(int(t[2]) for t in problems)
+        mp = max(int(t[3]) for t in problems)
+        rc = rq_tuxv_batched(self.h, prec, len(problems), d, mm, mn, mk, mb, mp, stream)
+        self._check(rc, "rq_tuxv_batched")
+        self._keep = d  # the descriptors must outlive the asynchronous launch
+        return outputs, info
 
     def qr(self, A, b, prec=None, stream=None):
         """In-place unpivoted blocked Householder QR of column-major A."""

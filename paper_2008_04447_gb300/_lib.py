@@ -45,7 +45,17 @@ _SIGS = {
     "rq_qr": ([_P, _I, _I, _I, _P, _I, _I, _P, _P, _P], _I),
     "rq_trqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _P, _P], _I),
     "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
+    "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
 }
+
+# rq_problem: twelve int32 then seven 64-bit device pointers (104 bytes)
+PROBLEM_FIELDS = ["m", "n", "k", "b", "p", "lda", "ldo", "ldu", "ldx", "ldv", "reserved0", "reserved1",
+                  "A", "Omega", "U", "X", "V", "sigma", "info"]
+
+
+def problem_dtype():
+    import numpy as np
+    return np.dtype([(f, np.int32) for f in PROBLEM_FIELDS[:12]] + [(f, np.uint64) for f in PROBLEM_FIELDS[12:]])
 
 _lib = None
 
@@ -149,6 +159,10 @@ def rq_rqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream
 def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
     return load().rq_rqrcp_noalloc(prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
                                    _ptr(info), _stream(stream))
+
+
+def rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, stream=None):
+    return load().rq_tuxv_batched(h, prec, count, _ptr(problems), max_m, max_n, max_k, max_b, max_p, _stream(stream))
 
 
 def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):

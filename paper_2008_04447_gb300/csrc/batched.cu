@@ -1,0 +1,569 @@
+// Batched truncated RQRCP + TUXV (Alg. 5 and Alg. 6, j_max = 1) for many
+// small, uneven problems in ONE persistent launch.
+//
+// Each CTA pulls problem indices from an atomic queue and runs the whole
+// factorisation of that problem: sketch, per block the sample QRCP, the panel,
+// the accumulated inner products W^T and the new rows of R, the sample update,
+// then the LQ / QR tail with explicit U and V.  Problems never wait for each
+// other, so uneven sizes balance dynamically (list the largest first).  The
+// per-problem scratch lives in one slot per CTA of a workspace sized for the
+// largest problem.  Storage and the contractions are FP32 (the sketch's inputs
+// rounded to BF16 in RQ_MIXED); Householder scalars (norms, beta, tau), the
+// downdated sample norms, T and the Omegahat_11 solve are FP64.
+#include <cmath>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rq {
+namespace {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int kMaxBB = 64;   // largest block size of the batched path
+constexpr int kMaxLB = 128;  // largest sample rank of the batched path
+
+__device__ __forceinline__ float bsum_f(float v, float* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t += red[w];
+  return t;
+}
+
+__device__ __forceinline__ double bsum_d(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t += red[w];
+  return t;
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// C (M x N) = alpha op(A) op(B) + beta C, FP32, block-level (all NT threads).
+// Shared scratch: 2 * 16 * (BM + BN + 2) floats.
+template <bool TA, bool TB, int BM, int BN, bool BF16>
+__device__ void bgemm(int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb, float beta,
+                      float* C, int ldc, float* sm) {
+  constexpr int BK = 16;
+  constexpr int RT = 16, CT = 16;  // thread grid
+  constexpr int TM = BM / RT, TN = BN / CT;
+  float* As = sm;                   // [BK][BM + 1]
+  float* Bs = sm + BK * (BM + 1);   // [BK][BN + 1]
+  const int tid = threadIdx.x;
+  const int tm = tid % RT, tn = tid / RT;
+  for (int i0 = 0; i0 < M; i0 += BM) {
+    for (int j0 = 0; j0 < N; j0 += BN) {
+      float acc[TM][TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += NT) {
+          int i, kk;
+          if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+          const int gi = i0 + i, gk = k0 + kk;
+          float v = 0.f;
+          if (gi < M && gk < K) v = TA ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda];
+          As[kk * (BM + 1) + i] = BF16 ? bf16_round(v) : v;
+        }
+        for (int e = tid; e < BK * BN; e += NT) {
+          int kk, j;
+          if (!TB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+          const int gk = k0 + kk, gj = j0 + j;
+          float v = 0.f;
+          if (gk < K && gj < N) v = TB ? B[gj + (size_t)gk * ldb] : B[gk + (size_t)gj * ldb];
+          Bs[kk * (BN + 1) + j] = BF16 ? bf16_round(v) : v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+          float av[TM], bv[TN];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) av[i] = As[kk * (BM + 1) + tm + i * RT];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) bv[j] = Bs[kk * (BN + 1) + tn + j * CT];
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int gj = j0 + tn + j * CT;
+        if (gj >= N) continue;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const int gi = i0 + tm + i * RT;
+          if (gi >= M) continue;
+          float* cp = C + gi + (size_t)gj * ldc;
+          float v = alpha * acc[i][j];
+          if (beta != 0.f) v = fmaf(beta, *cp, v);
+          *cp = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Dispatch on the output shape: skinny outputs use 32 x 128 tiles.
+template <bool TA, bool TB, bool BF16 = false>
+__device__ void gemm_b(int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb, float beta,
+                       float* C, int ldc, float* sm) {
+  if (M <= 0 || N <= 0) return;
+  if (M <= 32)
+    bgemm<TA, TB, 32, 128, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+  else if (N <= 32)
+    bgemm<TA, TB, 128, 32, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+  else
+    bgemm<TA, TB, 64, 64, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+}
+
+struct Shm {
+  double redd[NW];
+  float redf[NW];
+  double vv[kMaxLB];
+  double sc[4];
+  int si[4];
+  int wp[NW];
+  float dots[NW][kMaxBB];
+  float tw[kMaxBB];
+  double tvec[kMaxBB];
+};
+
+// Householder QR of the mt x bj panel P (column-major, ld ldp) in place; v below
+// the diagonal, R above; explicit Y (zeros above, unit diagonal) into Yout
+// (ld ldy); tau; T (bj x bj, ld ldt, FP64) by the compound WY rule.
+__device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy, float* tau, double* T, int ldt,
+                        Shm& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < bj * bj; e += NT) T[(e % bj) + (size_t)(e / bj) * ldt] = 0.0;
+  for (int j = 0; j < bj; ++j) {
+    float* aj = P + (size_t)j * ldp;
+    double x2 = 0.0;
+    for (int g = j + 1 + tid; g < mt; g += NT) x2 = fma((double)aj[g], (double)aj[g], x2);
+    x2 = bsum_d(x2, s.redd);
+    if (tid == 0) {
+      const double alpha = aj[j];
+      const double nrm2 = fma(alpha, alpha, x2);
+      double tu = 0.0, beta = 0.0, y1 = 1.0;
+      if (nrm2 > 0.0) {
+        const double nrm = sqrt(nrm2);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        y1 = alpha - beta;
+        tu = 2.0 / (1.0 + x2 / (y1 * y1));
+      }
+      s.sc[0] = tu;
+      s.sc[1] = y1;
+      s.sc[2] = beta;
+      tau[j] = (float)tu;
+    }
+    __syncthreads();
+    const double tu = s.sc[0], y1 = s.sc[1];
+    for (int g = j + 1 + tid; g < mt; g += NT) aj[g] = tu != 0.0 ? (float)((double)aj[g] / y1) : 0.f;
+    __syncthreads();
+    // d_c = sum_{g > j} v_g P(g, c) for every other column c of the panel
+    float d[kMaxBB];
+#pragma unroll
+    for (int c = 0; c < kMaxBB; ++c) d[c] = 0.f;
+    for (int g = j + 1 + tid; g < mt; g += NT) {
+      const float v = aj[g];
+#pragma unroll
+      for (int c = 0; c < kMaxBB; ++c)
+        if (c < bj && c != j) d[c] = fmaf(v, P[g + (size_t)c * ldp], d[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxBB; ++c) {
+      if (c >= bj) break;
+      const float t = warp_sum(d[c]);
+      if (lane == 0) s.dots[warp][c] = t;
+    }
+    __syncthreads();
+    if (tid < bj) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += s.dots[w][tid];
+      s.dots[0][tid] = t;
+    }
+    __syncthreads();
+    // w_c = P(j, c) + d_c for c > j; (Y^T v)_i = y_i(j) + d_i for i < j
+    if (tid > j && tid < bj) s.tw[tid] = (float)(tu * ((double)P[j + (size_t)tid * ldp] + (double)s.dots[0][tid]));
+    if (tid < j) s.tvec[tid] = (double)P[j + (size_t)tid * ldp] + (double)s.dots[0][tid];
+    __syncthreads();
+    // columns c > j: P(:, c) -= tau w_c v
+    for (int c = j + 1; c < bj; ++c) {
+      const float tw = s.tw[c];
+      float* ac = P + (size_t)c * ldp;
+      for (int g = j + tid; g < mt; g += NT) ac[g] = fmaf(-tw, g == j ? 1.f : aj[g], ac[g]);
+    }
+    // T(0:j, j) = -tau T(0:j, 0:j) (Y^T v)
+    if (tid < j) {
+      double acc = 0.0;
+      for (int q = tid; q < j; ++q) acc = fma(T[tid + (size_t)q * ldt], s.tvec[q], acc);
+      T[tid + (size_t)j * ldt] = -tu * acc;
+    }
+    if (tid == 0) {
+      T[j + (size_t)j * ldt] = tu;
+      aj[j] = (float)s.sc[2];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < mt * bj; e += NT) {
+    const int g = e % mt, c = e / mt;
+    Yout[g + (size_t)c * ldy] = g < c ? 0.f : (g == c ? 1.f : P[g + (size_t)c * ldp]);
+  }
+  __syncthreads();
+}
+
+// `steps` pivots from the l x nt sample B (ld l), exchanging columns in place
+// (B, jp, norms), downdating FP64 squared norms; S11 (FP64, ld lds) out.
+__device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, double* nu2, double* ref2, double* S11,
+                              int lds, Shm& s) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double tol = 1.4901161193847656e-08;
+  for (int c = tid; c < nt; c += NT) {
+    double acc = 0.0;
+    for (int r = 0; r < l; ++r) acc = fma((double)B[r + (size_t)c * l], (double)B[r + (size_t)c * l], acc);
+    nu2[c] = acc;
+    ref2[c] = acc;
+  }
+  __syncthreads();
+  for (int i = 0; i < steps; ++i) {
+    double bv = -1.0;
+    int bp = -1, dummy = 0;
+    for (int c = i + tid; c < nt; c += NT)
+      if (better(nu2[c], c, bv, bp)) { bv = nu2[c]; bp = c; }
+    warp_argmax(bv, bp, dummy);
+    if (lane == 0) { s.redd[warp] = bv; s.wp[warp] = bp; }
+    __syncthreads();
+    if (tid == 0) {
+      double gv = -1.0;
+      int gp = -1;
+      for (int w = 0; w < NW; ++w)
+        if (better(s.redd[w], s.wp[w], gv, gp)) { gv = s.redd[w]; gp = s.wp[w]; }
+      s.si[1] = gp;
+    }
+    __syncthreads();
+    const int p = s.si[1];
+    if (p != i) {
+      for (int r = tid; r < l; r += NT) {
+        const float t = B[r + (size_t)i * l];
+        B[r + (size_t)i * l] = B[r + (size_t)p * l];
+        B[r + (size_t)p * l] = t;
+      }
+      if (tid == 0) {
+        double t = nu2[i]; nu2[i] = nu2[p]; nu2[p] = t;
+        t = ref2[i]; ref2[i] = ref2[p]; ref2[p] = t;
+        const int ti = jp[i]; jp[i] = jp[p]; jp[p] = ti;
+      }
+    }
+    __syncthreads();
+    float* bi = B + (size_t)i * l;
+    if (warp == 0) {
+      double x2 = 0.0;
+      for (int r = i + 1 + lane; r < l; r += 32) x2 = fma((double)bi[r], (double)bi[r], x2);
+      x2 = warp_sum(x2);
+      const double alpha = bi[i];
+      const double nrm2 = fma(alpha, alpha, x2);
+      double beta = 0.0, y1 = 1.0;
+      const bool zero = !(nrm2 > 0.0);
+      if (!zero) {
+        const double nrm = sqrt(nrm2);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        y1 = alpha - beta;
+      }
+      for (int r = lane; r < steps; r += 32) S11[r + (size_t)i * lds] = r < i ? (double)bi[r] : (r == i ? beta : 0.0);
+      double v2 = 0.0;
+      for (int r = lane; r < l; r += 32) {
+        const double v = r < i ? 0.0 : (r == i ? 1.0 : (zero ? 0.0 : (double)bi[r] / y1));
+        s.vv[r] = v;
+        if (r > i) v2 = fma(v, v, v2);
+      }
+      v2 = warp_sum(v2);
+      if (lane == 0) { s.sc[0] = zero ? 0.0 : 2.0 / (1.0 + v2); s.sc[2] = beta; }
+    }
+    __syncthreads();
+    const float tu = (float)s.sc[0];
+    for (int c = i + 1 + tid; c < nt; c += NT) {
+      float* bc = B + (size_t)c * l;
+      if (tu != 0.f) {
+        float w = bc[i];
+        for (int r = i + 1; r < l; ++r) w = fmaf((float)s.vv[r], bc[r], w);
+        const float tw = tu * w;
+        bc[i] -= tw;
+        for (int r = i + 1; r < l; ++r) bc[r] = fmaf(-tw, (float)s.vv[r], bc[r]);
+      }
+      const double x = bc[i];
+      double nn = nu2[c] - x * x;
+      if (nn <= tol * ref2[c]) {
+        nn = 0.0;
+        for (int r = i + 1; r < l; ++r) nn = fma((double)bc[r], (double)bc[r], nn);
+        ref2[c] = nn;
+      }
+      nu2[c] = nn;
+    }
+    __syncthreads();
+    for (int r = tid; r < l; r += NT) bi[r] = r < i ? bi[r] : (r == i ? (float)s.sc[2] : 0.f);
+    __syncthreads();
+  }
+}
+
+struct Slot {
+  float *B, *Wt, *Z, *Y, *P, *Xt, *G, *Wsel, *taus, *Tf, *Zt, *Z1, *Yq, *YTq, *Wq, *tauq;
+  double *nu2, *ref2, *S11, *Oh, *T, *Tq;
+  int* jp;
+  size_t bytes;
+};
+
+__host__ __device__ inline Slot carve_slot(char* base, int m, int n, int k, int b, int l) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + 255) / 256 * 256;
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const int rmax = m > n ? m : n;
+  const int nb = (k + b - 1) / b;
+  Slot s;
+  s.B = (float*)take(sizeof(float) * (size_t)l * n);
+  s.Wt = (float*)take(sizeof(float) * (size_t)k * n);
+  s.Z = (float*)take(sizeof(float) * (size_t)k * n);
+  s.Y = (float*)take(sizeof(float) * (size_t)m * k);
+  s.P = (float*)take(sizeof(float) * (size_t)m * b);
+  s.Xt = (float*)take(sizeof(float) * (size_t)b * n);
+  s.G = (float*)take(sizeof(float) * (size_t)b * k);
+  s.Wsel = (float*)take(sizeof(float) * (size_t)k * b);
+  s.taus = (float*)take(sizeof(float) * (size_t)k);
+  s.Tf = (float*)take(sizeof(float) * (size_t)b * b);
+  s.Zt = (float*)take(sizeof(float) * (size_t)n * k);
+  s.Z1 = (float*)take(sizeof(float) * (size_t)m * k);
+  s.Yq = (float*)take(sizeof(float) * (size_t)rmax * k);
+  s.YTq = (float*)take(sizeof(float) * (size_t)rmax * b);
+  s.Wq = (float*)take(sizeof(float) * (size_t)b * k);
+  s.tauq = (float*)take(sizeof(float) * (size_t)k);
+  s.nu2 = (double*)take(sizeof(double) * (size_t)n);
+  s.ref2 = (double*)take(sizeof(double) * (size_t)n);
+  s.S11 = (double*)take(sizeof(double) * (size_t)b * b);
+  s.Oh = (double*)take(sizeof(double) * (size_t)b * b);
+  s.T = (double*)take(sizeof(double) * (size_t)b * b);
+  s.Tq = (double*)take(sizeof(double) * (size_t)nb * b * b);
+  s.jp = (int*)take(sizeof(int) * (size_t)n);
+  s.bytes = (off + 255) / 256 * 256;
+  return s;
+}
+
+__device__ void copy_T(const double* T, int ldt, int bj, float* Tf, int ldf) {
+  for (int e = threadIdx.x; e < bj * bj; e += NT) Tf[(e % bj) + (size_t)(e / bj) * ldf] = (float)T[(e % bj) + (size_t)(e / bj) * ldt];
+  __syncthreads();
+}
+
+// QR of the rows x k matrix M in place (block size b) with explicit Q(:, 1:k)
+// into Q (ld ldq) and, if Rout, R (k x k, upper) into Rout.
+__device__ void qr_explicit_b(float* M, int ldm, int rows, int k, int b, Slot& w, float* Q, int ldq, float* Rout,
+                              int ldr, Shm& s, float* sm) {
+  const int nb = (k + b - 1) / b;
+  for (int e = threadIdx.x; e < rows * k; e += NT) w.Yq[e] = 0.f;
+  __syncthreads();
+  for (int J = 0; J < nb; ++J) {
+    const int j0 = J * b, bj = min(b, k - j0), mt = rows - j0, n2 = k - j0 - bj;
+    float* Yj = w.Yq + j0 + (size_t)j0 * rows;
+    double* Tj = w.Tq + (size_t)J * b * b;
+    panel_b(M + j0 + (size_t)j0 * ldm, ldm, mt, bj, Yj, rows, w.tauq + j0, Tj, b, s);
+    if (n2 > 0) {
+      copy_T(Tj, b, bj, w.Tf, b);
+      float* M2 = M + j0 + (size_t)(j0 + bj) * ldm;
+      gemm_b<false, false>(mt, bj, bj, 1.f, Yj, rows, w.Tf, b, 0.f, w.YTq, mt, sm);
+      gemm_b<true, false>(bj, n2, mt, 1.f, w.YTq, mt, M2, ldm, 0.f, w.Wq, b, sm);
+      gemm_b<false, false>(mt, n2, bj, -1.f, Yj, rows, w.Wq, b, 1.f, M2, ldm, sm);
+    }
+  }
+  if (Rout) {
+    for (int e = threadIdx.x; e < k * k; e += NT) {
+      const int i = e % k, j = e / k;
+      Rout[i + (size_t)j * ldr] = i <= j ? M[i + (size_t)j * ldm] : 0.f;
+    }
+  }
+  for (int e = threadIdx.x; e < rows * k; e += NT) {
+    const int i = e % rows, j = e / rows;
+    Q[i + (size_t)j * ldq] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int J = nb - 1; J >= 0; --J) {
+    const int j0 = J * b, bj = min(b, k - j0), mt = rows - j0, nc = k - j0;
+    const float* Yj = w.Yq + j0 + (size_t)j0 * rows;
+    copy_T(w.Tq + (size_t)J * b * b, b, bj, w.Tf, b);
+    float* Qs = Q + j0 + (size_t)j0 * ldq;
+    gemm_b<true, false>(bj, nc, mt, 1.f, Yj, rows, Qs, ldq, 0.f, w.Wq, b, sm);
+    gemm_b<false, false>(bj, nc, bj, 1.f, w.Tf, b, w.Wq, b, 0.f, w.YTq, b, sm);
+    gemm_b<false, false>(mt, nc, bj, -1.f, Yj, rows, w.YTq, b, 1.f, Qs, ldq, sm);
+  }
+}
+
+struct BatchArgs {
+  const rq_problem* problems;
+  int count;
+  char* ws;
+  size_t slot_bytes;
+  int* counter;
+  int mixed;
+};
+
+__device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool mixed) {
+  const int m = pr.m, n = pr.n, k = pr.k, b = pr.b, l = pr.b + pr.p;
+  const float* A = static_cast<const float*>(pr.A);
+  const float* Om = static_cast<const float*>(pr.Omega);
+  const int lda = pr.lda;
+  const int tid = threadIdx.x;
+  for (int c = tid; c < n; c += NT) w.jp[c] = c;
+  for (int e = tid; e < m * k; e += NT) w.Y[e] = 0.f;
+  __syncthreads();
+  // sketch B = Omega A (BF16 inputs in the mixed precision mode)
+  if (mixed)
+    gemm_b<false, false, true>(l, n, m, 1.f, Om, pr.ldo, A, lda, 0.f, w.B, l, sm);
+  else
+    gemm_b<false, false, false>(l, n, m, 1.f, Om, pr.ldo, A, lda, 0.f, w.B, l, sm);
+  for (int j0 = 0; j0 < k; j0 += b) {
+    const int bj = min(b, k - j0), nt = n - j0, mt = m - j0, n2 = nt - bj;
+    float* BJ = w.B + (size_t)j0 * l;  // the live sample: columns j0.. (exchanged in place)
+    sample_qrcp_b(BJ, l, nt, bj, w.jp + j0, w.nu2 + j0, w.ref2 + j0, w.S11, b, s);
+    // selected columns of A - Y W^T
+    for (int e = tid; e < m * bj; e += NT) {
+      const int g = e % m, c = e / m;
+      w.P[g + (size_t)c * m] = A[g + (size_t)w.jp[j0 + c] * lda];
+    }
+    if (j0 > 0)
+      for (int e = tid; e < j0 * bj; e += NT) {
+        const int r = e % j0, c = e / j0;
+        w.Wsel[r + (size_t)c * k] = w.Wt[r + (size_t)w.jp[j0 + c] * k];
+      }
+    __syncthreads();
+    if (j0 > 0) gemm_b<false, false>(m, bj, j0, -1.f, w.Y, m, w.Wsel, k, 1.f, w.P, m, sm);
+    float* Y2 = w.Y + j0 + (size_t)j0 * m;
+    panel_b(w.P + j0, m, mt, bj, Y2, m, w.taus + j0, w.T, b, s);
+    copy_T(w.T, b, bj, w.Tf, b);
+    // W_2^T = T_2^T (Y_2^T A - (Y_2^T Y_1) W_1^T)
+    gemm_b<true, false>(bj, n, mt, 1.f, Y2, m, A + j0, lda, 0.f, w.Xt, b, sm);
+    if (j0 > 0) {
+      gemm_b<true, false>(bj, j0, mt, 1.f, Y2, m, w.Y + j0, m, 0.f, w.G, b, sm);
+      gemm_b<false, false>(bj, n, j0, -1.f, w.G, b, w.Wt, k, 1.f, w.Xt, b, sm);
+    }
+    gemm_b<true, false>(bj, n, bj, 1.f, w.Tf, b, w.Xt, b, 0.f, w.Wt + j0, k, sm);
+    // new rows of R (original column order)
+    for (int e = tid; e < bj * n; e += NT) {
+      const int r = e % bj, c = e / bj;
+      w.Z[j0 + r + (size_t)c * k] = A[j0 + r + (size_t)c * lda];
+    }
+    __syncthreads();
+    gemm_b<false, false>(bj, n, j0 + bj, -1.f, w.Y + j0, m, w.Wt, k, 1.f, w.Z + j0, k, sm);
+    for (int e = tid; e < bj * (j0 + bj); e += NT) {
+      const int r = e % bj, pos = e / bj;
+      float v = 0.f;
+      if (pos >= j0) {
+        const int c = pos - j0;
+        v = r <= c ? w.P[j0 + r + (size_t)c * m] : 0.f;
+      }
+      w.Z[j0 + r + (size_t)w.jp[pos] * k] = v;
+    }
+    __syncthreads();
+    if (j0 + bj < k) {
+      // Eq. (update1): Omegahat11 = S11 R11^{-1} (FP64), B1 = S12 - Omegahat11 R12
+      if (tid < bj) {
+        const int r = tid;
+        for (int j = 0; j < bj; ++j) {
+          double acc = j >= r ? w.S11[r + (size_t)j * b] : 0.0;
+          for (int i = r; i < j; ++i) acc -= w.Oh[r + (size_t)i * b] * (double)w.P[j0 + i + (size_t)j * m];
+          const double d = w.P[j0 + j + (size_t)j * m];
+          w.Oh[r + (size_t)j * b] = (j < r || d == 0.0) ? 0.0 : acc / d;
+        }
+      }
+      __syncthreads();
+      float* B1 = BJ + (size_t)bj * l;
+      for (int e = tid; e < bj * n2; e += NT) {
+        const int r = e % bj, t = e / bj;
+        const float* zc = w.Z + j0 + (size_t)w.jp[j0 + bj + t] * k;
+        double acc = 0.0;
+        for (int i = r; i < bj; ++i) acc = fma(w.Oh[r + (size_t)i * b], (double)zc[i], acc);
+        B1[r + (size_t)t * l] = (float)((double)B1[r + (size_t)t * l] - acc);
+      }
+      __syncthreads();
+    }
+  }
+  // TUXV tail: V from the LQ of Z0 = R P^T, Z1 = A V, QR of Z1 -> U, X
+  float* U = static_cast<float*>(pr.U);
+  float* X = static_cast<float*>(pr.X);
+  float* V = static_cast<float*>(pr.V);
+  for (int e = tid; e < k * n; e += NT) {
+    const int r = e % k, c = e / k;
+    w.Zt[c + (size_t)r * n] = w.Z[r + (size_t)c * k];
+  }
+  __syncthreads();
+  qr_explicit_b(w.Zt, n, n, k, b, w, V, pr.ldv, nullptr, 0, s, sm);
+  gemm_b<false, false>(m, k, n, 1.f, A, lda, V, pr.ldv, 0.f, w.Z1, m, sm);
+  qr_explicit_b(w.Z1, m, m, k, b, w, U, pr.ldu, X, pr.ldx, s, sm);
+  if (tid == 0 && pr.info) *pr.info = 0;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) tuxv_batched_kernel(BatchArgs a) {
+  extern __shared__ float sm[];
+  __shared__ Shm s;
+  __shared__ int s_idx;
+  char* base = a.ws + (size_t)blockIdx.x * a.slot_bytes;
+  while (true) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= a.count) break;
+    const rq_problem pr = a.problems[idx];
+    if (pr.sigma != nullptr) {  // the core SVD is not part of the batched path
+      if (threadIdx.x == 0 && pr.info) *pr.info = RQ_ENOTIMPL;
+      continue;
+    }
+    Slot w = carve_slot(base, pr.m, pr.n, pr.k, pr.b, pr.b + pr.p);
+    solve_one(pr, w, s, sm, a.mixed != 0);
+  }
+}
+
+}  // namespace
+
+size_t batched_slot_bytes(int max_m, int max_n, int max_k, int max_b, int max_p) {
+  return carve_slot(nullptr, max_m, max_n, max_k, max_b, max_b + max_p).bytes;
+}
+
+int batched_limits_ok(int max_b, int max_p) { return max_b >= 1 && max_b <= kMaxBB && max_b + max_p <= kMaxLB; }
+
+cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
+                         int* counter, bool mixed) {
+  const size_t smem = 2 * 16 * (128 + 32 + 2) * sizeof(float);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
+  if (e != cudaSuccess) return e;
+  BatchArgs a{problems, count, ws, slot_bytes, counter, mixed ? 1 : 0};
+  tuxv_batched_kernel<<<slots, NT, smem, c.stream>>>(a);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+int batched_slots(int num_sms) {
+  int per_sm = 0;
+  const size_t smem = 2 * 16 * (128 + 32 + 2) * sizeof(float);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tuxv_batched_kernel, NT, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * num_sms;
+}
+
+}  // namespace rq

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 
+#include "../../include/rqrcp.h"
+
 namespace rq {
 
 struct Ctx {
@@ -11,12 +13,31 @@ struct Ctx {
   long long* launches;  // launch counter of the handle
   int* err;             // device error word (RQ_ETIMEOUT from bounded waits)
   unsigned int* bar;    // device grid barrier {count, generation}
+  void* splitk = nullptr;       // scratch for split-K partial products (nullptr: no split)
+  size_t splitk_bytes = 0;
 };
 
 // C = alpha * op(A) * op(B) + beta * C, column-major (SIMT tiles).
 template <typename T>
 cudaError_t gemm(const Ctx& c, bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda,
                  const T* B, int ldb, T beta, T* C, int ldc);
+
+// C = A B with both inputs rounded to BF16 (products exact in FP32), FP32
+// accumulation: the reduced-precision sketch.
+cudaError_t gemm_bf16_inputs(const Ctx& c, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                             float* C, int ldc);
+
+// C (M x N) = alpha * sum_z P_z + beta * C, z in order (P_z: M x N, stride pzs).
+cudaError_t splitk_reduce_f32(const Ctx& c, int M, int N, int S, const float* P, size_t pzs, float alpha, float beta,
+                              float* C, int ldc);
+
+// Tensor-core FP32 GEMM, C = alpha A^T B + beta C (A: K x M, B: K x N, column-major,
+// i.e. both K-major), 3xTF32 when split3; C^T stored when transC.  Needs
+// 16-byte aligned bases and leading dimensions that are multiples of 4
+// (tc_gemm_supported); splits K through c.splitk when the tiles are few.
+bool tc_gemm_supported(const float* A, int lda, const float* B, int ldb);
+cudaError_t tc_gemm_tn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
+                       int ldb, float beta, float* C, int ldc, bool transC, bool split3);
 
 // Partial QRCP of the sample (l x nt): `steps` pivots, norms downdated.
 // Writes S11 (steps x steps, FP64, ld lds), swaps[steps], src[nt] (old position
@@ -52,6 +73,52 @@ cudaError_t omegahat11(const Ctx& c, const double* S11, int lds, const TS* R11, 
 template <typename TS>
 cudaError_t sample_update(const Ctx& c, int bj, int n2, const double* Oh, int ldo, const TS* R12,
                           int ldr, TS* B1, int ldb);
+
+// dst(:, i) = src(:, idx[i]), i < count (rows entries per column).
+template <typename TS>
+cudaError_t gather_columns(const Ctx& c, const TS* src, int lds, int rows, const int* idx, int count, TS* dst,
+                           int ldd);
+
+// The permutation of permute_columns applied to an index vector only.
+cudaError_t permute_index(const Ctx& c, int steps, const int* chg, const int* src, int* v, int* tmp);
+
+// TRQRCP: in the new rows Zb (bj x n, original column order) set the columns
+// chosen in earlier blocks (positions < j0) to zero and the block's own
+// columns (positions j0..j0+bj-1) to R11 (upper triangle of R11, ld ldr).
+template <typename TS>
+cudaError_t trq_fix_new_rows(const Ctx& c, TS* Zb, int ldz, int bj, int j0, const int* jpvt, const TS* R11,
+                             int ldr);
+
+// B1 (bj x n2) -= Oh * R12 with R12(:, t) = Zb(:, idx[t]).
+template <typename TS>
+cudaError_t sample_update_idx(const Ctx& c, int bj, int n2, const double* Oh, int ldo, const TS* Zb, int ldz,
+                              const int* idx, TS* B1, int ldb);
+
+// TUXV tail helpers.
+template <typename TS>
+cudaError_t transpose(const Ctx& c, int rows, int cols, const TS* s, int lds, TS* d, int ldd);
+template <typename TS>
+cudaError_t set_eye(const Ctx& c, int rows, int cols, TS* d, int ldd);
+template <typename TS>
+cudaError_t copy_upper(const Ctx& c, int k, const TS* s, int lds, TS* d, int ldd);
+// One-sided Jacobi SVD of the k x k X: X = Uh diag(sigma) Vh^T, sigma descending.
+// scratch: jacobi_scratch_doubles(k); rot: max_sweeps ints.
+size_t jacobi_scratch_doubles(int k);
+template <typename TS>
+cudaError_t jacobi_svd(const Ctx& c, int k, const TS* X, int ldx, TS* Uh, int ldu, TS* Vh, int ldv, TS* sigma,
+                       double* scratch, int* rot, int max_sweeps);
+// Make the largest-magnitude entry of each column of V positive (U follows).
+template <typename TS>
+cudaError_t fix_signs(const Ctx& c, int m, int n, int k, TS* U, int ldu, TS* V, int ldv);
+template <typename TS>
+cudaError_t set_diag(const Ctx& c, int k, const TS* s, TS* X, int ldx);
+
+// Batched TRQRCP + TUXV (persistent, one CTA per problem at a time).
+size_t batched_slot_bytes(int max_m, int max_n, int max_k, int max_b, int max_p);
+int batched_limits_ok(int max_b, int max_p);
+int batched_slots(int num_sms);
+cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
+                         int* counter, bool mixed);
 
 cudaError_t iota(const Ctx& c, int* v, int n);
 // info = RQ_ETIMEOUT if the device error word is set, else the first j with

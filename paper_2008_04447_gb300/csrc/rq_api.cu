@@ -107,8 +107,13 @@ struct FactorWs {
   TS *B0, *B1, *Ybuf, *YT, *Wt, *ptmp, *Tts;
   double *S11, *Oh, *T, *cand, *pscr;
   int *jtmp, *chg, *swaps, *src;
+  char* splitk;
+  size_t splitk_bytes;
   size_t bytes;
 };
+
+// Split-K partials of the b x n W^T product: up to 8 partial copies.
+inline size_t splitk_bytes_for(int b, int n, size_t elem) { return 8 * (size_t)b * n * elem; }
 
 template <typename TS>
 FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
@@ -132,6 +137,8 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
   w.src = c.take<int>((size_t)n);
   w.cand = c.take<double>(sample_qrcp_scratch_doubles(l, num_sms));
   w.pscr = c.take<double>(panel_scratch_doubles(b, num_sms));
+  w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS));
+  w.splitk = c.take<char>(w.splitk_bytes);
   w.bytes = align_up(c.off, 256);
   return w;
 }
@@ -165,7 +172,7 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
   int rc = ensure_ws(h, w.bytes);
   if (rc) return rc;
   w = carve_factor<TS>(h->ws, m, n, b, l, h->num_sms);
-  Ctx c{st, h->num_sms, &h->launches, w.err, w.bar};
+  Ctx c{st, h->num_sms, &h->launches, w.err, w.bar, w.splitk, w.splitk_bytes};
   cudaError_t e = cudaMemsetAsync(w.bar, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
   if (jpvt && (e = iota(c, jpvt, n)) != cudaSuccess) return cuda_fail(h, e, "iota");
@@ -239,6 +246,316 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
   return RQ_OK;
 }
 
+// Workspace of truncated RQRCP (Alg. 5).
+template <typename TS>
+struct TruncWs {
+  unsigned int* bar;
+  int* err;
+  TS *B0, *B1, *Tts, *Wt, *Z, *P, *Wsel, *G, *X;
+  double *S11, *Oh, *T, *cand, *pscr;
+  int *jtmp, *chg, *swaps, *src;
+  char* splitk;
+  size_t splitk_bytes;
+  size_t bytes;
+};
+
+template <typename TS>
+TruncWs<TS> carve_trunc(void* base, int m, int n, int k, int b, int l, int num_sms) {
+  Carver c(base);
+  TruncWs<TS> w;
+  w.bar = c.take<unsigned int>(4);
+  w.err = reinterpret_cast<int*>(w.bar + 2);
+  w.B0 = c.take<TS>((size_t)l * n);
+  w.B1 = c.take<TS>((size_t)l * n);
+  w.S11 = c.take<double>((size_t)b * b);
+  w.Oh = c.take<double>((size_t)b * b);
+  w.T = c.take<double>((size_t)b * b);
+  w.Tts = c.take<TS>((size_t)b * b);
+  w.Wt = c.take<TS>((size_t)k * n);
+  w.Z = c.take<TS>((size_t)k * n);
+  w.P = c.take<TS>((size_t)m * b);
+  w.Wsel = c.take<TS>((size_t)k * b);
+  w.G = c.take<TS>((size_t)b * k);
+  w.X = c.take<TS>((size_t)b * n);
+  w.jtmp = c.take<int>((size_t)2 * b);
+  w.chg = c.take<int>((size_t)2 * b);
+  w.swaps = c.take<int>((size_t)b);
+  w.src = c.take<int>((size_t)n);
+  w.cand = c.take<double>(sample_qrcp_scratch_doubles(l, num_sms));
+  w.pscr = c.take<double>(panel_scratch_doubles(b, num_sms));
+  w.splitk_bytes = splitk_bytes_for(b > k ? b : k, n, sizeof(TS));
+  w.splitk = c.take<char>(w.splitk_bytes);
+  w.bytes = align_up(c.off, 256);
+  return w;
+}
+
+// Truncated RQRCP without trailing update, Alg. 5.  A is never written.  The
+// accumulated inner products W^T = T^T Y^T A and the finished rows of R are
+// kept in A's ORIGINAL column order (Z = R P^T), so no large array is ever
+// permuted: the selected columns are gathered through jpvt, and the pivoted R
+// is gathered once at the end.
+template <typename TS>
+cudaError_t sketch_gemm(const Ctx& c, bool mixed, int l, int n, int m, const TS* Omega, int ldo, const TS* A, int lda,
+                        TS* B) {
+  if constexpr (sizeof(TS) == sizeof(float)) {
+    if (mixed) return gemm_bf16_inputs(c, l, n, m, Omega, ldo, A, lda, B, l);
+  }
+  return gemm<TS>(c, false, false, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), B, l);
+}
+
+template <typename TS>
+int run_trqrcp(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, int k, const TS* Omega, int ldo,
+               TS* Y, int ldy, TS* tau, TS* R, int ldr, int* jpvt, int* info, cudaStream_t st, TS** Z_out,
+               TruncWs<TS>* ws_out, bool mixed = false) {
+  const int l = b + p;
+  TruncWs<TS> w = carve_trunc<TS>(nullptr, m, n, k, b, l, h->num_sms);
+  int rc = ensure_ws(h, w.bytes);
+  if (rc) return rc;
+  w = carve_trunc<TS>(h->ws, m, n, k, b, l, h->num_sms);
+  Ctx c{st, h->num_sms, &h->launches, w.err, w.bar, w.splitk, w.splitk_bytes};
+  const double sz = sizeof(TS);
+  cudaError_t e = cudaMemsetAsync(w.bar, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(TS), 0, (size_t)m * sizeof(TS), k, st);
+  if (e == cudaSuccess) e = iota(c, jpvt, n);
+  if (e != cudaSuccess) return cuda_fail(h, e, "trqrcp setup");
+  TS* Bc = w.B0;
+  TS* Bn = w.B1;
+  {
+    Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * l * (double)m * n, sz * ((double)m * n + (double)l * m + (double)l * n));
+    e = sketch_gemm<TS>(c, mixed, l, n, m, Omega, ldo, A, lda, Bc);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sketch");
+  }
+  for (int j0 = 0; j0 < k; j0 += b) {
+    const int bj = (k - j0) < b ? (k - j0) : b;
+    const int nt = n - j0, mt = m - j0, n2 = nt - bj;
+    {
+      Phase ph(h, st, RQ_PHASE_SAMPLE_QRCP, 4.0 * l * (double)nt * bj, 2.0 * sz * l * (double)nt);
+      e = sample_qrcp<TS>(c, Bc, l, l, nt, bj, Bn, l, w.S11, b, w.swaps, w.src, w.chg, w.cand);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sample_qrcp");
+    }
+    {
+      Phase ph(h, st, RQ_PHASE_PERMUTE, 0.0, 2.0 * sz * bj * (double)m);
+      e = permute_index(c, bj, w.chg, w.src, jpvt + j0, w.jtmp);
+      // selected columns of A - Y^[J-1] W_1^T (Alg. 5 "construct selected columns")
+      if (e == cudaSuccess) e = gather_columns<TS>(c, A, lda, m, jpvt + j0, bj, w.P, m);
+      if (e != cudaSuccess) return cuda_fail(h, e, "gather");
+    }
+    if (j0 > 0) {
+      Phase ph(h, st, RQ_PHASE_OTHER, 2.0 * m * (double)j0 * bj, sz * ((double)m * j0 + 2.0 * m * bj));
+      e = gather_columns<TS>(c, w.Wt, k, j0, jpvt + j0, bj, w.Wsel, k);
+      if (e == cudaSuccess) e = gemm<TS>(c, false, false, m, bj, j0, TS(-1), Y, ldy, w.Wsel, k, TS(1), w.P, m);
+      if (e != cudaSuccess) return cuda_fail(h, e, "selected columns");
+    }
+    {
+      Phase ph(h, st, RQ_PHASE_PANEL, 2.0 * (double)mt * bj * bj, 2.0 * sz * (double)mt * bj);
+      e = panel_qr<TS>(c, w.P + j0, m, mt, bj, tau + j0, Y + j0 + (size_t)j0 * ldy, ldy, w.T, b, w.pscr);
+      if (e != cudaSuccess) return cuda_fail(h, e, "panel");
+    }
+    const TS* Tm;
+    if (sizeof(TS) == sizeof(double)) {
+      Tm = reinterpret_cast<const TS*>(w.T);
+    } else {
+      e = convert<TS, double>(c, bj, bj, w.T, b, w.Tts, b);
+      if (e != cudaSuccess) return cuda_fail(h, e, "convert T");
+      Tm = w.Tts;
+    }
+    const TS* Y2 = Y + j0 + (size_t)j0 * ldy;  // rows j0.. of the block's reflectors
+    {
+      // W_2^T = T_2^T (Y_2^T A - (Y_2^T Y_1) W_1^T)  (Alg. 5, "form inner products")
+      Phase ph(h, st, RQ_PHASE_TRAILING,
+               2.0 * bj * (double)mt * n + 2.0 * bj * (double)mt * j0 + 2.0 * bj * (double)j0 * n +
+                   2.0 * bj * (double)bj * n,
+               sz * ((double)mt * n + (double)mt * (bj + j0) + (double)(j0 + 2 * bj) * n));
+      e = gemm<TS>(c, true, false, bj, n, mt, TS(1), Y2, ldy, A + j0, lda, TS(0), w.X, b);
+      if (e == cudaSuccess && j0 > 0) {
+        e = gemm<TS>(c, true, false, bj, j0, mt, TS(1), Y2, ldy, Y + j0, ldy, TS(0), w.G, b);
+        if (e == cudaSuccess) e = gemm<TS>(c, false, false, bj, n, j0, TS(-1), w.G, b, w.Wt, k, TS(1), w.X, b);
+      }
+      if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, n, bj, TS(1), Tm, b, w.X, b, TS(0), w.Wt + j0, k);
+      if (e != cudaSuccess) return cuda_fail(h, e, "inner products");
+    }
+    {
+      // new rows of R from A - Y W^T (original column order)
+      Phase ph(h, st, RQ_PHASE_OTHER, 2.0 * bj * (double)(j0 + bj) * n,
+               sz * (2.0 * bj * (double)n + (double)(j0 + bj) * n + (double)bj * (j0 + bj)));
+      e = convert<TS, TS>(c, bj, n, A + j0, lda, w.Z + j0, k);
+      if (e == cudaSuccess)
+        e = gemm<TS>(c, false, false, bj, n, j0 + bj, TS(-1), Y + j0, ldy, w.Wt, k, TS(1), w.Z + j0, k);
+      if (e == cudaSuccess) e = trq_fix_new_rows<TS>(c, w.Z + j0, k, bj, j0, jpvt, w.P + j0, m);
+      if (e != cudaSuccess) return cuda_fail(h, e, "R rows");
+    }
+    if (j0 + bj < k) {
+      Phase ph(h, st, RQ_PHASE_SAMPLE_UPDATE, (double)bj * bj * bj / 3.0 + (double)bj * bj * n2,
+               sz * 3.0 * bj * (double)n2);
+      e = omegahat11<TS>(c, w.S11, b, w.P + j0, m, bj, w.Oh, b);
+      if (e == cudaSuccess) e = sample_update_idx<TS>(c, bj, n2, w.Oh, b, w.Z + j0, k, jpvt + j0 + bj, Bn, l);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sample update");
+    }
+    TS* t = Bc;
+    Bc = Bn;
+    Bn = t;
+  }
+  {
+    Phase ph(h, st, RQ_PHASE_OTHER, 0.0, 2.0 * sz * k * (double)n);
+    if (R) {
+      e = gather_columns<TS>(c, w.Z, k, k, jpvt, n, R, ldr);
+      if (e == cudaSuccess) e = finish_info<TS>(c, R, ldr, k, info);
+    } else {
+      e = finish_info<TS>(c, w.P, m, 0, info);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "R gather");
+  }
+  if (Z_out) *Z_out = w.Z;
+  if (ws_out) *ws_out = w;
+  return RQ_OK;
+}
+
+// Blocked Householder QR of a tall rows x k matrix M (in place) with the
+// explicit Q(:, 1:k) formed by applying the block reflectors backwards to
+// [I; 0] and the upper triangular R copied out (Alg. 6's QR / LQ steps).
+template <typename TS>
+struct QrScratch {
+  TS *Yall, *YT, *Wt, *Tts, *tau;
+  double *Tall, *pscr;
+};
+
+template <typename TS>
+cudaError_t qr_explicit(const Ctx& c, TS* M, int ldm, int rows, int k, int b, const QrScratch<TS>& s, TS* Q, int ldq,
+                        TS* Rout, int ldr) {
+  cudaError_t e = cudaMemset2DAsync(s.Yall, (size_t)rows * sizeof(TS), 0, (size_t)rows * sizeof(TS), k, c.stream);
+  const int nb = (k + b - 1) / b;
+  for (int J = 0; J < nb && e == cudaSuccess; ++J) {
+    const int j0 = J * b, bj = (k - j0) < b ? (k - j0) : b, mt = rows - j0, n2 = k - j0 - bj;
+    TS* Yj = s.Yall + j0 + (size_t)j0 * rows;
+    double* Tj = s.Tall + (size_t)J * b * b;
+    e = panel_qr<TS>(c, M + j0 + (size_t)j0 * ldm, ldm, mt, bj, s.tau + j0, Yj, rows, Tj, b, s.pscr);
+    if (e != cudaSuccess || n2 <= 0) continue;
+    const TS* Tm = reinterpret_cast<const TS*>(Tj);
+    if (sizeof(TS) != sizeof(double)) {
+      e = convert<TS, double>(c, bj, bj, Tj, b, s.Tts, b);
+      Tm = s.Tts;
+    }
+    TS* M2 = M + j0 + (size_t)(j0 + bj) * ldm;
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), Yj, rows, Tm, b, TS(0), s.YT, mt);
+    if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, n2, mt, TS(1), s.YT, mt, M2, ldm, TS(0), s.Wt, b);
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, n2, bj, TS(-1), Yj, rows, s.Wt, b, TS(1), M2, ldm);
+  }
+  if (e == cudaSuccess && Rout) e = copy_upper<TS>(c, k, M, ldm, Rout, ldr);
+  if (e == cudaSuccess) e = set_eye<TS>(c, rows, k, Q, ldq);
+  for (int J = nb - 1; J >= 0 && e == cudaSuccess; --J) {
+    const int j0 = J * b, bj = (k - j0) < b ? (k - j0) : b, mt = rows - j0, nc = k - j0;
+    const TS* Yj = s.Yall + j0 + (size_t)j0 * rows;
+    const double* Tj = s.Tall + (size_t)J * b * b;
+    const TS* Tm = reinterpret_cast<const TS*>(Tj);
+    if (sizeof(TS) != sizeof(double)) {
+      e = convert<TS, double>(c, bj, bj, Tj, b, s.Tts, b);
+      Tm = s.Tts;
+    }
+    TS* Qs = Q + j0 + (size_t)j0 * ldq;
+    // Qs <- (I - Y T Y^T) Qs
+    if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, nc, mt, TS(1), Yj, rows, Qs, ldq, TS(0), s.Wt, b);
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, bj, nc, bj, TS(1), Tm, b, s.Wt, b, TS(0), s.YT, b);
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, nc, bj, TS(-1), Yj, rows, s.YT, b, TS(1), Qs, ldq);
+  }
+  return e;
+}
+
+// TUXV workspace: the TRQRCP workspace followed by the tail's buffers.
+template <typename TS>
+struct TuxvWs {
+  TruncWs<TS> tr;
+  TS *Ytr, *taut, *Zt, *Z1, *Uh, *Vh, *Tmp;
+  QrScratch<TS> qs;
+  double* jac;
+  int *rot, *jp;
+  size_t bytes;
+};
+
+constexpr int kMaxSweeps = 40;
+
+template <typename TS>
+TuxvWs<TS> carve_tuxv(void* base, int m, int n, int k, int b, int l, int num_sms) {
+  TuxvWs<TS> w;
+  w.tr = carve_trunc<TS>(base, m, n, k, b, l, num_sms);
+  Carver c(base);
+  c.off = w.tr.bytes;
+  const int rows = m > n ? m : n;
+  const int nb = (k + b - 1) / b;
+  w.Ytr = c.take<TS>((size_t)m * k);
+  w.taut = c.take<TS>((size_t)k);
+  w.Zt = c.take<TS>((size_t)n * k);
+  w.Z1 = c.take<TS>((size_t)m * k);
+  w.Uh = c.take<TS>((size_t)k * k);
+  w.Vh = c.take<TS>((size_t)k * k);
+  w.Tmp = c.take<TS>((size_t)rows * k);
+  w.qs.Yall = c.take<TS>((size_t)rows * k);
+  w.qs.YT = c.take<TS>((size_t)rows * b);
+  w.qs.Wt = c.take<TS>((size_t)b * k);
+  w.qs.Tts = c.take<TS>((size_t)b * b);
+  w.qs.tau = c.take<TS>((size_t)k);
+  w.qs.Tall = c.take<double>((size_t)nb * b * b);
+  w.qs.pscr = c.take<double>(panel_scratch_doubles(b, num_sms));
+  w.jac = c.take<double>(jacobi_scratch_doubles(k));
+  w.rot = c.take<int>(kMaxSweeps);
+  w.jp = c.take<int>((size_t)n);
+  w.bytes = align_up(c.off, 256);
+  return w;
+}
+
+// TUXV, Alg. 6 with j_max = 1: TRQRCP -> Z0 = R P^T -> LQ of Z0 (QR of Z0^T,
+// V explicit) -> Z1 = A V -> QR of Z1 (U explicit, X = R) -> optional core SVD.
+template <typename TS>
+int run_tuxv(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, int k, const TS* Omega, int ldo, TS* U,
+             int ldu, TS* X, int ldx, TS* V, int ldv, TS* sigma, int* info, cudaStream_t st, bool mixed = false) {
+  const int l = b + p;
+  TuxvWs<TS> w = carve_tuxv<TS>(nullptr, m, n, k, b, l, h->num_sms);
+  int rc = ensure_ws(h, w.bytes);
+  if (rc) return rc;
+  w = carve_tuxv<TS>(h->ws, m, n, k, b, l, h->num_sms);
+  // the TRQRCP part carves the same prefix of the workspace and leaves Z = R P^T there
+  int* jp = w.jp;  // the column permutation P0 of TRQRCP (absorbed into V, not an output)
+  TS* Z = nullptr;
+  rc = run_trqrcp<TS>(h, m, n, A, lda, b, p, k, Omega, ldo, w.Ytr, m, w.taut, nullptr, k, jp, info, st, &Z, nullptr,
+                      mixed);
+  if (rc) return rc;
+  Ctx c{st, h->num_sms, &h->launches, w.tr.err, w.tr.bar, w.tr.splitk, w.tr.splitk_bytes};
+  const double sz = sizeof(TS);
+  cudaError_t e;
+  {
+    // LQ of Z0 = R P^T through the QR of its transpose: V = Q(:, 1:k)
+    Phase ph(h, st, RQ_PHASE_OTHER, 4.0 * n * (double)k * k, sz * 6.0 * n * (double)k);
+    e = transpose<TS>(c, k, n, Z, k, w.Zt, n);
+    if (e == cudaSuccess) e = qr_explicit<TS>(c, w.Zt, n, n, k, b, w.qs, V, ldv, nullptr, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "LQ of Z0");
+  }
+  {
+    // Z1 = A V(:, 1:k): one more pass over A (Alg. 6)
+    Phase ph(h, st, RQ_PHASE_TRAILING, 2.0 * m * (double)n * k, sz * ((double)m * n + (double)n * k + (double)m * k));
+    e = gemm<TS>(c, false, false, m, k, n, TS(1), A, lda, V, ldv, TS(0), w.Z1, m);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Z1 = A V");
+  }
+  {
+    Phase ph(h, st, RQ_PHASE_OTHER, 4.0 * m * (double)k * k, sz * 6.0 * m * (double)k);
+    e = qr_explicit<TS>(c, w.Z1, m, m, k, b, w.qs, U, ldu, X, ldx);
+    if (e != cudaSuccess) return cuda_fail(h, e, "QR of Z1");
+  }
+  if (sigma) {
+    // core SVD of X: U <- U Uh, V <- V Vh, X <- diag(sigma)
+    Phase ph(h, st, RQ_PHASE_OTHER, 2.0 * (double)(m + n) * k * k, sz * 2.0 * (double)(m + n) * k);
+    e = jacobi_svd<TS>(c, k, X, ldx, w.Uh, k, w.Vh, k, sigma, w.jac, w.rot, kMaxSweeps);
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, m, k, k, TS(1), U, ldu, w.Uh, k, TS(0), w.Tmp, m);
+    if (e == cudaSuccess) e = convert<TS, TS>(c, m, k, w.Tmp, m, U, ldu);
+    if (e == cudaSuccess) e = gemm<TS>(c, false, false, n, k, k, TS(1), V, ldv, w.Vh, k, TS(0), w.Tmp, n);
+    if (e == cudaSuccess) e = convert<TS, TS>(c, n, k, w.Tmp, n, V, ldv);
+    if (e == cudaSuccess) e = fix_signs<TS>(c, m, n, k, U, ldu, V, ldv);
+    if (e == cudaSuccess) e = set_diag<TS>(c, k, sigma, X, ldx);
+    if (e != cudaSuccess) return cuda_fail(h, e, "core SVD");
+  }
+  e = finish_info<TS>(c, X, ldx, 0, info);
+  if (e != cudaSuccess) return cuda_fail(h, e, "info");
+  return RQ_OK;
+}
+
 int check_common(rq_handle h, int prec) {
   if (!valid(h)) return RQ_EHANDLE;
   if (prec != RQ_FP64 && prec != RQ_FP32 && prec != RQ_MIXED) return -2;
@@ -298,7 +615,18 @@ int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b,
                              : carve_factor<float>(nullptr, m, n, b, l, h->num_sms).bytes;
     return RQ_OK;
   }
-  (void)k;
+  if (op == RQ_OP_TUXV) {
+    if (k < 1) return -6;
+    *bytes = prec == RQ_FP64 ? carve_tuxv<double>(nullptr, m, n, k, b, l, h->num_sms).bytes
+                             : carve_tuxv<float>(nullptr, m, n, k, b, l, h->num_sms).bytes;
+    return RQ_OK;
+  }
+  if (op == RQ_OP_TRQRCP) {
+    if (k < 1) return -6;
+    *bytes = prec == RQ_FP64 ? carve_trunc<double>(nullptr, m, n, k, b, l, h->num_sms).bytes
+                             : carve_trunc<float>(nullptr, m, n, k, b, l, h->num_sms).bytes;
+    return RQ_OK;
+  }
   return RQ_ENOTIMPL;
 }
 
@@ -407,19 +735,94 @@ int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* ta
 
 int rq_trqrcp(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k, const void* Omega,
               int ldo, void* Y, int ldy, void* tau, void* R, int ldr, int* jpvt, int* info, rq_stream stream) {
-  (void)prec; (void)m; (void)n; (void)A; (void)lda; (void)b; (void)p; (void)k; (void)Omega; (void)ldo;
-  (void)Y; (void)ldy; (void)tau; (void)R; (void)ldr; (void)jpvt; (void)info; (void)stream;
-  if (!valid(h)) return RQ_EHANDLE;
-  return fail(h, RQ_ENOTIMPL, "rq_trqrcp: not built yet");
+  int rc = check_common(h, prec);
+  if (rc) return rc;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (!A) return -5;
+  if (lda < m) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (k < 1 || k > (m < n ? m : n)) return -9;
+  if (!Omega) return -10;
+  if (ldo < b + p) return -11;
+  if (!Y) return -12;
+  if (ldy < m) return -13;
+  if (!tau) return -14;
+  if (!R) return -15;
+  if (ldr < k) return -16;
+  if (!jpvt) return -17;
+  if (!info) return -18;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == RQ_FP64)
+    return run_trqrcp<double>(h, m, n, static_cast<const double*>(A), lda, b, p, k,
+                              static_cast<const double*>(Omega), ldo, static_cast<double*>(Y), ldy,
+                              static_cast<double*>(tau), static_cast<double*>(R), ldr, jpvt, info, st, nullptr,
+                              nullptr);
+  return run_trqrcp<float>(h, m, n, static_cast<const float*>(A), lda, b, p, k, static_cast<const float*>(Omega), ldo,
+                           static_cast<float*>(Y), ldy, static_cast<float*>(tau), static_cast<float*>(R), ldr, jpvt,
+                           info, st, nullptr, nullptr, prec == RQ_MIXED);
 }
 
 int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k, const void* Omega,
             int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv, void* sigma, int* info,
             rq_stream stream) {
-  (void)prec; (void)m; (void)n; (void)A; (void)lda; (void)b; (void)p; (void)k; (void)Omega; (void)ldo;
-  (void)U; (void)ldu; (void)X; (void)ldx; (void)V; (void)ldv; (void)sigma; (void)info; (void)stream;
+  int rc = check_common(h, prec);
+  if (rc) return rc;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (!A) return -5;
+  if (lda < m) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (k < 1 || k > (m < n ? m : n)) return -9;
+  if (!Omega) return -10;
+  if (ldo < b + p) return -11;
+  if (!U) return -12;
+  if (ldu < m) return -13;
+  if (!X) return -14;
+  if (ldx < k) return -15;
+  if (!V) return -16;
+  if (ldv < n) return -17;
+  if (!info) return -19;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == RQ_FP64)
+    return run_tuxv<double>(h, m, n, static_cast<const double*>(A), lda, b, p, k, static_cast<const double*>(Omega),
+                            ldo, static_cast<double*>(U), ldu, static_cast<double*>(X), ldx, static_cast<double*>(V),
+                            ldv, static_cast<double*>(sigma), info, st);
+  return run_tuxv<float>(h, m, n, static_cast<const float*>(A), lda, b, p, k, static_cast<const float*>(Omega), ldo,
+                         static_cast<float*>(U), ldu, static_cast<float*>(X), ldx, static_cast<float*>(V), ldv,
+                         static_cast<float*>(sigma), info, st, prec == RQ_MIXED);
+}
+
+int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,
+                    int max_b, int max_p, rq_stream stream) {
   if (!valid(h)) return RQ_EHANDLE;
-  return fail(h, RQ_ENOTIMPL, "rq_tuxv: not built yet");
+  if (prec != RQ_FP32 && prec != RQ_MIXED) return prec == RQ_FP64 ? fail(h, RQ_ENOTIMPL, "batched FP64") : -2;
+  if (count < 0) return -3;
+  if (count > 0 && !problems) return -4;
+  if (max_m < 1) return -5;
+  if (max_n < 1) return -6;
+  if (max_k < 1 || max_k > (max_m < max_n ? max_m : max_n)) return -7;
+  if (!batched_limits_ok(max_b, 0)) return -8;
+  if (max_p < 0 || !batched_limits_ok(max_b, max_p)) return -9;
+  if (count == 0) return RQ_OK;
+  const int slots = batched_slots(h->num_sms);
+  const size_t slot = batched_slot_bytes(max_m, max_n, max_k, max_b, max_p);
+  const size_t need = 256 + (size_t)slots * slot;
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  char* base = static_cast<char*>(h->ws);
+  int* counter = reinterpret_cast<int*>(base);
+  unsigned int* bar = reinterpret_cast<unsigned int*>(base + 16);
+  Ctx c{static_cast<cudaStream_t>(stream), h->num_sms, &h->launches, reinterpret_cast<int*>(base + 32), bar};
+  cudaError_t e;
+  {
+    Phase ph(h, c.stream, RQ_PHASE_OTHER, 0.0, 0.0);
+    e = tuxv_batched(c, count, problems, base + 256, slot, slots, counter, prec == RQ_MIXED);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "rq_tuxv_batched");
+  return RQ_OK;
 }
 
 }  // extern "C"

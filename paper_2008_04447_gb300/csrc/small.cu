@@ -74,6 +74,69 @@ __global__ void sample_update_kernel(int bj, int n2, const double* __restrict__ 
   }
 }
 
+// dst(:, i) = src(:, idx[i]) for i < count (rows x count, column-major).
+template <typename TS>
+__global__ void gather_cols_kernel(const TS* __restrict__ src, int lds, int rows, const int* __restrict__ idx,
+                                   int count, TS* __restrict__ dst, int ldd) {
+  const int i = blockIdx.y;
+  if (i >= count) return;
+  const TS* s = src + (size_t)idx[i] * lds;
+  TS* d = dst + (size_t)i * ldd;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) d[r] = s[r];
+}
+
+__global__ void index_gather(const int* __restrict__ chg, const int* __restrict__ src, const int* __restrict__ v,
+                             int* __restrict__ tmp, int slots) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= slots) return;
+  const int e = chg[t];
+  if (e >= 0) tmp[t] = v[src[e]];
+}
+
+__global__ void index_scatter(const int* __restrict__ chg, const int* __restrict__ tmp, int* __restrict__ v,
+                              int slots) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= slots) return;
+  const int e = chg[t];
+  if (e >= 0) v[e] = tmp[t];
+}
+
+// New rows j0..j0+bj-1 of Z = R P^T (original column order): the columns chosen
+// in earlier blocks are zero there; the block's own columns take R11 from the panel.
+template <typename TS>
+__global__ void trq_fix_rows(TS* __restrict__ Zb, int ldz, int bj, int j0, const int* __restrict__ jpvt,
+                             const TS* __restrict__ R11, int ldr) {
+  const int pos = blockIdx.x;  // < j0 + bj
+  const int col = jpvt[pos];
+  for (int r = threadIdx.x; r < bj; r += blockDim.x) {
+    TS v = TS(0);
+    if (pos >= j0) {
+      const int c = pos - j0;
+      v = r <= c ? R11[r + (size_t)c * ldr] : TS(0);
+    }
+    Zb[r + (size_t)col * ldz] = v;
+  }
+}
+
+// B1(:, t) -= Oh * Z(:, idx[t]) (K = bj), FP64 accumulation.
+template <typename TS>
+__global__ void sample_update_idx_kernel(int bj, int n2, const double* __restrict__ Oh, int ldo,
+                                         const TS* __restrict__ Zb, int ldz, const int* __restrict__ idx,
+                                         TS* __restrict__ B1, int ldb) {
+  extern __shared__ double sO[];
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) sO[e] = Oh[(e % bj) + (size_t)(e / bj) * ldo];
+  __syncthreads();
+  const int col = blockIdx.x;
+  if (col >= n2) return;
+  const TS* rc = Zb + (size_t)idx[col] * ldz;
+  TS* bc = B1 + (size_t)col * ldb;
+  for (int r = threadIdx.x; r < bj; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], static_cast<double>(rc[i]), acc);
+    bc[r] = static_cast<TS>(static_cast<double>(bc[r]) - acc);
+  }
+}
+
 __global__ void iota_kernel(int* v, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
 }
@@ -140,6 +203,45 @@ cudaError_t sample_update(const Ctx& c, int bj, int n2, const double* Oh, int ld
   return cudaGetLastError();
 }
 
+template <typename TS>
+cudaError_t gather_columns(const Ctx& c, const TS* src, int lds, int rows, const int* idx, int count, TS* dst,
+                           int ldd) {
+  if (rows <= 0 || count <= 0) return cudaSuccess;
+  int bx = (rows + 255) / 256;
+  if (bx > 64) bx = 64;
+  gather_cols_kernel<TS><<<dim3(bx, count), 256, 0, c.stream>>>(src, lds, rows, idx, count, dst, ldd);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t permute_index(const Ctx& c, int steps, const int* chg, const int* src, int* v, int* tmp) {
+  if (steps <= 0) return cudaSuccess;
+  const int slots = 2 * steps;
+  index_gather<<<(slots + 127) / 128, 128, 0, c.stream>>>(chg, src, v, tmp, slots);
+  index_scatter<<<(slots + 127) / 128, 128, 0, c.stream>>>(chg, tmp, v, slots);
+  *c.launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t trq_fix_new_rows(const Ctx& c, TS* Zb, int ldz, int bj, int j0, const int* jpvt, const TS* R11,
+                             int ldr) {
+  trq_fix_rows<TS><<<j0 + bj, 64, 0, c.stream>>>(Zb, ldz, bj, j0, jpvt, R11, ldr);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t sample_update_idx(const Ctx& c, int bj, int n2, const double* Oh, int ldo, const TS* Zb, int ldz,
+                              const int* idx, TS* B1, int ldb) {
+  if (n2 <= 0) return cudaSuccess;
+  const int threads = bj <= 32 ? 32 : (bj <= 64 ? 64 : (bj <= 128 ? 128 : 256));
+  sample_update_idx_kernel<TS><<<n2, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(bj, n2, Oh, ldo, Zb,
+                                                                                             ldz, idx, B1, ldb);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
 cudaError_t iota(const Ctx& c, int* v, int n) {
   iota_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, c.stream>>>(v, n);
   ++*c.launches;
@@ -168,7 +270,11 @@ cudaError_t convert(const Ctx& c, int rows, int cols, const TS* src, int lds, TD
                                            int*);                                                            \
   template cudaError_t omegahat11<TS>(const Ctx&, const double*, int, const TS*, int, int, double*, int);    \
   template cudaError_t sample_update<TS>(const Ctx&, int, int, const double*, int, const TS*, int, TS*, int); \
-  template cudaError_t finish_info<TS>(const Ctx&, const TS*, int, int, int*);
+  template cudaError_t finish_info<TS>(const Ctx&, const TS*, int, int, int*);                              \
+  template cudaError_t gather_columns<TS>(const Ctx&, const TS*, int, int, const int*, int, TS*, int);       \
+  template cudaError_t trq_fix_new_rows<TS>(const Ctx&, TS*, int, int, int, const int*, const TS*, int);      \
+  template cudaError_t sample_update_idx<TS>(const Ctx&, int, int, const double*, int, const TS*, int,        \
+                                             const int*, TS*, int);
 RQ_INST(double)
 RQ_INST(float)
 template cudaError_t convert<float, double>(const Ctx&, int, int, const double*, int, float*, int);

@@ -1,0 +1,381 @@
+// FP32 GEMM on the 5th-generation tensor cores: C = alpha * A^T B + beta * C
+// with 3xTF32 error compensation (or plain TF32).
+//
+// A is K x M and B is K x N, both column-major, so both operands are K-major
+// ("TN" form); this is the natural layout for every large FP32 product of the
+// RQRCP/TRQRCP/TUXV path (the block reflector's W^T = (YT)^T A2, its update
+// A2 -= Y W^T with Y^T kept K-major, the TRQRCP products Y2^T A).
+//
+// Per CTA: one 128 x BN output tile, accumulated in TMEM.
+//   warp 0      : TMA producer (128B-swizzled BK=32 slices of A and B)
+//   warp 1      : TMEM allocation and the single-thread tcgen05.mma issue
+//   warps 2..5  : split each landed slice into TF32 hi / lo parts in place
+//                 (x = hi + lo exactly, hi rounded to TF32), then the epilogue
+//                 (tcgen05.ld -> registers -> C)
+// For each BK slice: Ahi*Bhi + Ahi*Blo + Alo*Bhi, four K=8 MMAs per product.
+// All waits are bounded; on a timeout the kernel records RQ_ETIMEOUT, lets
+// its copies land, frees its TMEM and returns.
+#include <cuda.h>
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rq {
+namespace {
+
+constexpr int TBM = 128;  // tile rows (M) = TMEM lanes
+constexpr int TBK = 32;   // K slice: 32 FP32 = one 128-byte swizzle row
+constexpr int kTcThreads = 192;
+constexpr long long kWaitLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase of parity `par` to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par, int* err) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(par)
+        : "memory");
+    if (ok) return true;
+    if ((i & 1023) == 1023 && *reinterpret_cast<volatile int*>(err) != 0) return false;
+  }
+  atomicCAS(err, 0, RQ_ETIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t tf32_idesc(int bn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+struct TcArgs {
+  int M, N, K;       // full problem
+  int kchunk;        // K range of blockIdx.z
+  float alpha, beta;
+  float* C;
+  int ldc;
+  int transC;        // store C^T (C is N x M)
+  size_t czs;        // blockIdx.z stride of C (split-K partials)
+  int split3;        // 3xTF32 (1) or plain TF32 (0)
+  int* err;
+};
+
+template <int BN, int NS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  constexpr uint32_t ABYTES = TBM * TBK * 4;
+  constexpr uint32_t BBYTES = BN * TBK * 4;
+  constexpr uint32_t STAGE = 2 * ABYTES + 2 * BBYTES;  // hi and lo copies of both slices
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bars[3 * NS + 1];
+  __shared__ uint32_t s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * a.kchunk;
+  const int kend = min(a.K, kbeg + a.kchunk);
+  const int nk = (kend - kbeg + TBK - 1) / TBK;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto ready = [&](int s) { return bar0 + 8u * (NS + s); };
+  auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
+  const uint32_t done = bar0 + 8u * (3 * NS);
+  auto a_hi = [&](int s) { return sm + (size_t)s * STAGE; };
+  auto a_lo = [&](int s) { return sm + (size_t)s * STAGE + ABYTES; };
+  auto b_hi = [&](int s) { return sm + (size_t)s * STAGE + 2 * ABYTES; };
+  auto b_lo = [&](int s) { return sm + (size_t)s * STAGE + 2 * ABYTES + BBYTES; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(ready(s), 128);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < nk && ok; ++it) {
+        const int s = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(empty(s), ph ^ 1, a.err)) { ok = false; break; }
+        mbar_expect_tx(full(s), ABYTES + BBYTES);
+        tma_load_2d(smem_u32(a_hi(s)), &mapA, kbeg + it * TBK, m0, full(s));
+        tma_load_2d(smem_u32(b_hi(s)), &mapB, kbeg + it * TBK, n0, full(s));
+        issued = it + 1;
+      }
+      // let the copies still in flight land before the CTA may exit
+      for (int it = (issued > NS ? issued - NS : 0); it < issued; ++it)
+        mbar_wait(full(it % NS), (it / NS) & 1, a.err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tf32_idesc(BN);
+      bool ok = true;
+      for (int it = 0; it < nk && ok; ++it) {
+        const int s = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(ready(s), ph, a.err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(a_hi(s)), al = smem_u32(a_lo(s));
+        const uint32_t bh = smem_u32(b_hi(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+        for (int kk = 0; kk < TBK / 8; ++kk) {
+          const uint32_t off = kk * 32;
+          const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bh + off), idesc, acc);
+          if (a.split3) {
+            mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1u);
+            mma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1u);
+          }
+        }
+        mma_commit(empty(s));
+      }
+      mma_commit(done);
+    }
+  } else {
+    // warps 2..5: split slices into hi / lo, then the epilogue
+    const int t = threadIdx.x - 64;
+    bool ok = true;
+    for (int it = 0; it < nk && ok; ++it) {
+      const int s = it % NS;
+      const uint32_t ph = (it / NS) & 1;
+      if (!mbar_wait(full(s), ph, a.err)) { ok = false; break; }
+      if (a.split3) {
+        float4* ah = reinterpret_cast<float4*>(a_hi(s));
+        float4* al = reinterpret_cast<float4*>(a_lo(s));
+        for (int e = t; e < (int)(ABYTES / 16); e += 128) {
+          float4 x = ah[e], h, l;
+          h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
+          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+          ah[e] = h;
+          al[e] = l;
+        }
+        float4* bh = reinterpret_cast<float4*>(b_hi(s));
+        float4* bl = reinterpret_cast<float4*>(b_lo(s));
+        for (int e = t; e < (int)(BBYTES / 16); e += 128) {
+          float4 x = bh[e], h, l;
+          h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
+          l.x = x.x - h.x; l.y = x.y - h.y; l.z = x.z - h.z; l.w = x.w - h.w;
+          bh[e] = h;
+          bl[e] = l;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(ready(s));
+    }
+    const bool have = ok && mbar_wait(done, 0, a.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (have) {
+      const int q = warp & 3;  // TMEM lane quarter this warp may read
+      const int row = m0 + q * 32 + lane;
+      float* C = a.C + blockIdx.z * a.czs;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < a.M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < a.N) {
+              float* cp = a.transC ? C + col + (size_t)row * a.ldc : C + row + (size_t)col * a.ldc;
+              float v = a.alpha * __uint_as_float(r[j]);
+              if (a.beta != 0.f) v = fmaf(a.beta, *cp, v);
+              *cp = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D K-major map over a column-major (rows = K) matrix: box {32, box_rows}.
+bool make_map(CUtensorMap* map, const float* base, int K, int cols, int ld, int box_rows) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)TBK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int NS>
+size_t tc_smem() {
+  return (size_t)NS * (2 * TBM * TBK * 4 + 2 * BN * TBK * 4) + 1024;
+}
+
+template <int BN, int NS>
+cudaError_t tc_launch(const Ctx& c, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, dim3 grid) {
+  const size_t smem = tc_smem<BN, NS>();
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tc_gemm_kernel<BN, NS><<<grid, kTcThreads, smem, c.stream>>>(ma, mb, args);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_supported(const float* A, int lda, const float* B, int ldb) {
+  return encoder() != nullptr && (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+         (reinterpret_cast<uintptr_t>(B) % 16 == 0) && lda % 4 == 0 && ldb % 4 == 0;
+}
+
+cudaError_t tc_gemm_tn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
+                       int ldb, float beta, float* C, int ldc, bool transC, bool split3) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!tc_gemm_supported(A, lda, B, ldb)) return cudaErrorNotSupported;
+  const int bn = N <= 64 ? 64 : 128;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, K, M, lda, TBM) || !make_map(&mb, B, K, N, ldb, bn)) return cudaErrorInvalidValue;
+  const int tiles = ((M + TBM - 1) / TBM) * ((N + bn - 1) / bn);
+  int S = 1;
+  if (c.splitk && tiles < 2 * c.num_sms && K >= 1024) {
+    S = (2 * c.num_sms + tiles - 1) / tiles;
+    if (S > K / 512) S = K / 512;
+    const size_t cap = c.splitk_bytes / (sizeof(float) * (size_t)M * N);
+    if ((size_t)S > cap) S = (int)cap;
+    if (S < 2) S = 1;
+  }
+  int kchunk = K;
+  if (S > 1) {
+    kchunk = ((K + S - 1) / S + TBK - 1) / TBK * TBK;
+    S = (K + kchunk - 1) / kchunk;
+  }
+  TcArgs args;
+  args.M = M;
+  args.N = N;
+  args.K = K;
+  args.kchunk = kchunk;
+  args.split3 = split3 ? 1 : 0;
+  args.err = c.err;
+  if (S == 1) {
+    args.alpha = alpha;
+    args.beta = beta;
+    args.C = C;
+    args.ldc = ldc;
+    args.transC = transC ? 1 : 0;
+    args.czs = 0;
+  } else {
+    // partials: P_z (rows x cols as finally stored), reduced in z order
+    args.alpha = 1.f;
+    args.beta = 0.f;
+    args.C = static_cast<float*>(c.splitk);
+    args.transC = transC ? 1 : 0;
+    args.ldc = transC ? N : M;
+    args.czs = (size_t)M * N;
+  }
+  dim3 grid((M + TBM - 1) / TBM, (N + bn - 1) / bn, S);
+  cudaError_t e = bn == 64 ? tc_launch<64, 4>(c, ma, mb, args, grid) : tc_launch<128, 3>(c, ma, mb, args, grid);
+  if (e != cudaSuccess || S == 1) return e;
+  return splitk_reduce_f32(c, transC ? N : M, transC ? M : N, S, static_cast<const float*>(c.splitk),
+                           (size_t)M * N, alpha, beta, C, ldc);
+}
+
+}  // namespace rq

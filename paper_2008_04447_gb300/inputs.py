@@ -89,7 +89,22 @@ def batch_shapes(count: int, seed: int, m_range=(64, 2048), n_cap=1024, k_range=
 
 def _torch():
     import torch
+    _preload_linalg(torch)
     return torch
+
+
+def _preload_linalg(torch):
+    """Load torch's CUDA linear-algebra library by path before its first use.
+
+    torch opens it lazily by name; under some profilers' injection that lookup
+    fails, so it is opened here once, globally, from torch's own lib folder.
+    """
+    import ctypes
+    import os
+    lib = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(lib) and not getattr(_preload_linalg, "done", False):
+        ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
+        _preload_linalg.done = True
 
 
 def omega_torch(l: int, m: int, seed: int, device="cuda", dtype=None):

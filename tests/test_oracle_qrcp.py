@@ -75,3 +75,19 @@ def test_sample_qrcp_downdating_recomputes_when_cancellation():
     assert sq.recomputed >= 1
     # after one step, column 2 (norm ~0.245) must beat column 1 (~1e-9)
     assert sq.perm[1] == 2
+
+
+def test_round_bf16_matches_definition():
+    """bfloat16 keeps the top 16 bits of a float32, rounded to nearest even."""
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9, -3.14159, 0.0, 1e-30])
+    r = O.round_bf16(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0 + 2 ** -7 or r[1] == 1.0  # exactly halfway between 1 and 1+2^-7
+    assert r[1] == 1.0                           # ties to even mantissa
+    assert r[2] == 1.0                           # below half an ulp (ulp = 2^-7)
+    assert r[3] == 1.0 + 2 ** -7                 # above half an ulp
+    assert abs(r[4] - (-3.140625)) < 1e-12       # -3.14159 -> nearest bf16
+    assert r[5] == 0.0
+    g = I.rng(3).standard_normal(1000)
+    rel = np.abs(O.round_bf16(g) - g) / np.abs(g)
+    assert rel.max() <= 2 ** -8 * (1 + 1e-6)
