@@ -40,9 +40,16 @@ def parse():
     ap.add_argument("--b", type=int, default=64)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--decades", type=float, default=12.0)
-    ap.add_argument("--no-extras", action="store_true", help="skip QR / FP32 / e2e / CPU legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg but the timed RQRCP")
+    ap.add_argument("--legs", default="qr,e2e,fp32,cpu,tuxv,batched,serving",
+                    help="extra legs to run (comma list); --no-extras clears it")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the timed RQRCP")
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
     ap.add_argument("--cpu-n", type=int, default=2048)
-    return ap.parse_args()
+    ap.add_argument("--batch", type=int, default=4096, help="problems in the batched leg")
+    args = ap.parse_args()
+    args.legs = set() if args.no_extras else {x.strip() for x in args.legs.split(",") if x.strip()}
+    return args
 
 
 def flops_qr(m, n):
@@ -114,11 +121,13 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """Max of a per-rank timing over all ranks (the slowest replica sets the pace)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -136,6 +145,150 @@ def cpu_baseline(n, b, p, decades):
     return {"value": flops_qr(n, n) / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"oracle RQRCP of one {n}x{n} FP64 graded matrix (10^-{decades:g} spread), b={b}, p={p}: "
                       f"{dt:.1f} s; numpy with its BLAS threads"}
+
+
+def batch_inputs(count, seed, threads=16):
+    """The many-small-problems workload: graded spectra 10^(-6 i/n), Haar factors,
+    (m, n, k) from the batch recipe; generated on the host (FP64) in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2008_04447_gb300 import inputs as I
+    shapes = I.batch_shapes(count, seed)
+
+    def one(i):
+        m, n, k = shapes[i]
+        b = min(32, k)
+        return (I.graded(m, n, 6, seed=seed * 100000 + i), I.omega(b + 8, m, seed=seed * 100000 + 50000 + i), b, 8, k)
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, range(count)))
+
+
+def to_device_f32(host):
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    return [(colmajor(torch.as_tensor(a, dtype=torch.float32)).cuda(),
+             colmajor(torch.as_tensor(om, dtype=torch.float32)).cuda(), b, p, k) for a, om, b, p, k in host]
+
+
+def leg_tuxv(h, steps=3, warmup=3):
+    """Truncated RQRCP + TUXV of one 32768 x 16384 matrix (low rank + noise), k = 512."""
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED, colmajor
+    from paper_2008_04447_gb300 import inputs as I
+    m, n, k, b, p = 32768, 16384, 512, 64, 8
+    A = colmajor(I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7).float())
+    Om = colmajor(I.omega_torch(b + p, m, seed=8, dtype=torch.float32))
+    for _ in range(warmup):
+        h.tuxv(A, Om, b, p, k, prec=RQ_MIXED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.profile(True)
+    e0.record()
+    for _ in range(steps):
+        U, X, V, _, info = h.tuxv(A, Om, b, p, k, prec=RQ_MIXED)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = h.profile_read()
+    h.profile(False)
+    ms = e0.elapsed_time(e1) / steps
+    # rank-k error in FP64 against the FP64 input: ||A||^2 - ||X||^2 (A V V^T is a projection)
+    A64 = I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7)
+    na2 = float((A64 * A64).sum())
+    Ud, Xd, Vd = U.double(), X.double(), V.double()
+    R = A64 - Ud @ (Xd @ Vd.T)
+    err = float(torch.linalg.norm(R)) / na2 ** 0.5
+    flops = 4.0 * k * m * n + 2.0 * (b + p) * m * n
+    tr = prof["trailing"]
+    out = {"workload": f"tuxv_mixed_lowrank_plus_noise_{m}x{n}_k{k}_b{b}_p{p}", "s": ms / 1e3,
+           "tflops": flops / (ms / 1e3) / 1e12, "rel_error": err,
+           "phases_ms": {kk: v[0] / steps for kk, v in prof.items()},
+           "hbm_bytes_algorithmic": 4.0 * m * n * (2 + k // b), "gbs_algorithmic": 4.0 * m * n * (2 + k // b) / (ms / 1e3) / 1e9,
+           "trailing_tflops": tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None}
+    del A, A64, R
+    return out
+
+
+def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24):
+    """4096 uneven problems in one persistent launch (mixed precision)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2008_04447_gb300 import RQ_MIXED
+    order = sorted(range(len(dev)), key=lambda i: -(dev[i][0].shape[0] * dev[i][0].shape[1] * dev[i][4]))
+    probs = [dev[i] for i in order]
+    outs, info = h.tuxv_batched(probs, prec=RQ_MIXED)
+    for _ in range(warmup - 1):
+        h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        outs, info = h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = sum(4.0 * k * A.shape[0] * A.shape[1] + 2.0 * (b + p) * A.shape[0] * A.shape[1] for A, Om, b, p, k in probs)
+    byts = sum(4.0 * A.shape[0] * A.shape[1] * (3 + (k + b - 1) // b) for A, Om, b, p, k in probs)
+    # error ratio against the FP64 oracle on a sample of problems
+    ratios = []
+    g = np.random.default_rng(0)
+    for j in g.choice(len(probs), size=min(oracle_sample, len(probs)), replace=False):
+        a, om, b, p, k = host[order[j]]
+        if a.shape[0] * a.shape[1] > 600 * 400:
+            continue
+        U, X, V = (t.cpu().double().numpy() for t in outs[j])
+        ref = O.tuxv(a, om, b, k)
+        e_gpu = np.linalg.norm(a - U @ X @ V.T)
+        e_ref = np.linalg.norm(a - ref.U @ ref.X @ ref.V.T)
+        ratios.append(e_gpu / e_ref)
+    return {"workload": f"batched_tuxv_mixed_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
+            "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
+            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "info_nonzero": int((info != 0).sum()),
+            "error_ratio_vs_fp64_oracle": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
+                                           "max": float(np.max(ratios)) if ratios else None}}
+
+
+def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9):
+    """Poisson arrivals of TUXV requests: the batch mix plus 10% 8192 x 4096, k = 256."""
+    import numpy as np
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    from paper_2008_04447_gb300 import inputs as I
+    from paper_2008_04447_gb300.serve import Server
+    big = [(colmajor(I.lowrank_plus_noise_torch(8192, 4096, 1024, 1e-6, seed=40 + i).float()),
+            colmajor(I.omega_torch(72, 8192, seed=50 + i, dtype=torch.float32)), 64, 8, 256) for i in range(2)]
+    results = []
+    g = np.random.default_rng(1)
+    for rate in rates:
+        srv = Server(budget_bytes=budget, lanes=3)
+        # warm the lanes' workspaces
+        for lane_h, st in srv.lanes:
+            lane_h.tuxv_batched(dev[:8], stream=st)
+            lane_h.tuxv(*big[0][:2], 64, 8, 256, stream=st)
+        torch.cuda.synchronize()
+        srv.start()
+        n = max(20, int(rate * seconds))
+        gaps = g.exponential(1.0 / rate, size=n)
+        t0 = time.perf_counter()
+        tnext = t0
+        reqs = []
+        for i in range(n):
+            tnext += gaps[i]
+            while time.perf_counter() < tnext:
+                pass
+            if g.random() < large_frac:
+                A, Om, b, p, k = big[i % len(big)]
+            else:
+                A, Om, b, p, k = dev[int(g.integers(len(dev)))]
+            reqs.append(srv.submit(A, Om, b, p, k))
+        for r in reqs:
+            r.wait(120)
+        srv.stop()
+        st_ = srv.stats()
+        st_["offered_rate"] = rate
+        results.append(st_)
+        torch.cuda.synchronize()
+    return {"workload": "poisson TUXV requests: 90% batch mix (m<=2048, n<=1024, k<=128), 10% 8192x4096 k=256",
+            "budget_gb": budget / 1e9, "by_rate": results}
 
 
 def run_reference(args, ws, rank):
@@ -173,6 +326,10 @@ def main():
     if rank == 0:
         B.build()
     barrier(ws)
+    if args.only_batched:
+        host = batch_inputs(args.batch, seed=0)
+        print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), oracle_sample=0)}), flush=True)
+        return
     n, b, p = args.n, args.b, args.p
     m = n
     l = b + p
@@ -180,6 +337,9 @@ def main():
 
     A0 = colmajor(I.graded_torch(m, n, args.decades, seed=rank))          # pristine FP64 input
     Om = colmajor(I.omega_torch(l, m, seed=1000 + rank))
+    if args.prec == "fp32":
+        A0 = colmajor(A0.float())
+        Om = colmajor(Om.float())
     A = torch.empty_like(A0)
     torch.cuda.synchronize()
     h = Handle()
@@ -227,15 +387,21 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"rqrcp_fp64_graded_{m}x{n}_b{b}_p{p}", "m": m, "n": n, "b": b, "p": p, "k": n,
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": f"rqrcp_{args.prec}_graded_{m}x{n}_b{b}_p{p}", "m": m, "n": n, "b": b, "p": p, "k": n,
                        "spectrum": f"U diag(10^(-{args.decades:g} i/n)) V^T, Haar U, V",
                        "l2": "inputs larger than L2 (A is 2.1 GB)",
                        "step": "device copy restoring A (2.1 GB) + rq_rqrcp", "parallelism": f"replicas x{ws}"},
             "rqrcp_s": ms_step / 1e3, "roofline": roofline, "phases": phases, "gpu_launches": launches,
             "clocks": clocks}
 
-    if rank == 0 and not args.no_extras:
+    if args.prec == "fp32":
+        roofline.update({"bound": "hbm", "peak": 6793.1, "unit": "GB/s", "achieved": tr[2] / (tr[0] / 1e3) / 1e9,
+                         "kernel": "trailing update (tensor-core 3xTF32 GEMMs), FP32",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"})
+        roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    legs = args.legs if rank == 0 else set()
+    if "qr" in legs:
         # unpivoted blocked QR of the same matrix, same kernels (the paper's comparison)
         def qr_step():
             A.copy_(A0)
@@ -253,12 +419,13 @@ def main():
         line["qr"] = {"s": qr_ms / 1e3, "tflops": fl / (qr_ms / 1e3) / 1e12,
                       "rqrcp_over_qr": ms_step / qr_ms}
 
+    if "e2e" in legs:
         # end to end through the C ABI with host buffers (pinned; column-major A is
         # copied as its contiguous transpose so each copy is one cudaMemcpyAsync)
-        Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+        Ah = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
         Ah.copy_(A0.t())
-        Ao = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
-        tau_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        Ao = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
+        tau_h = torch.empty(n, dtype=A0.dtype, pin_memory=True)
         jp_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
 
         def e2e_step():
@@ -275,10 +442,12 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / E
-        line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * m * n,
-                       "d2h_bytes_per_step": 8 * m * n + 12 * n, "s_per_step": e2e_s}
+        esz = A0.element_size()
+        line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
+                       "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": e2e_s}
         del Ah, Ao
 
+    if "fp32" in legs and args.prec == "fp64":
         # FP32 path on the same matrix (FP32 storage and updates, FP64 reflectors and norms)
         A32 = A0.float()
         A32 = colmajor(A32)
@@ -310,7 +479,21 @@ def main():
                         "qr_tflops": fl / (q32 / 1e3) / 1e12, "rqrcp_over_qr": r32 / q32}
         del A32, W
 
+    if "cpu" in legs:
         line["cpu_baseline"] = cpu_baseline(args.cpu_n, b, p, args.decades)
+    del A0, A
+    torch.cuda.empty_cache()
+    if "tuxv" in legs:
+        line["tuxv"] = leg_tuxv(h)
+        torch.cuda.empty_cache()
+    if "batched" in legs or "serving" in legs:
+        host = batch_inputs(args.batch, seed=0)
+        dev = to_device_f32(host)
+        if "batched" in legs:
+            line["batched"] = leg_batched(h, host, dev)
+        if "serving" in legs:
+            line["serving"] = leg_serving(dev)
+        del dev
     barrier(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)

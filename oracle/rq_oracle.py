@@ -262,6 +262,7 @@ class RQRCPResult:
     gaps: list = field(default_factory=list)      # per block: decision gaps
     samples: list = field(default_factory=list)   # per block: the sample used (if kept)
     omegahat: list = field(default_factory=list)  # explicit mode: (Omegahat, S, R11) per block
+    sample_norms: list = field(default_factory=list)  # ||B||_F of the sample used by each block
     info: int = 0
 
 
@@ -295,6 +296,7 @@ def rqrcp(A, Omega, b, k=None, mode="update", keep_samples=False, resample=None,
                 res.samples.append(B.copy())
             sq = sample_qrcp(B, bj)
             res.gaps.append(sq.gaps)
+            res.sample_norms.append(float(np.linalg.norm(B)))
             F[:, j0:] = F[:, j0:][:, sq.perm]   # permute A and completed rows of R
             jpvt[j0:] = jpvt[j0:][sq.perm]
         # b reflectors of the panel, then Q^T applied to the trailing columns
@@ -354,6 +356,7 @@ class TRQRCPResult:
     Wt: np.ndarray         # k x n accumulated inner products W^T = T^T Y^T A P
     k: int
     gaps: list = field(default_factory=list)
+    sample_norms: list = field(default_factory=list)
     info: int = 0
 
 
@@ -387,8 +390,10 @@ def trqrcp(A, Omega, b, k, sketch_inputs=None):
     tau = np.zeros(k)
     gaps = []
     B = sketch(Omega, Ap, sketch_inputs)
+    norms = []
     for j0 in range(0, k, b):
         bj = min(b, k - j0)
+        norms.append(float(np.linalg.norm(B)))
         sq = sample_qrcp(B, bj)
         gaps.append(sq.gaps)
         # permute A^[J], W_1^T and the leading rows of R
@@ -416,7 +421,7 @@ def trqrcp(A, Omega, b, k, sketch_inputs=None):
             B = sample_update(sq.S, bj, R[j0:j0 + bj, j0:j0 + bj], R[j0:j0 + bj, j0 + bj:])
     d = np.abs(np.diag(R[:, :k]))
     zero = np.nonzero(d == 0.0)[0]
-    return TRQRCPResult(Y, tau, R, jpvt, Wt, k, gaps, int(zero[0]) + 1 if zero.size else 0)
+    return TRQRCPResult(Y, tau, R, jpvt, Wt, k, gaps, norms, int(zero[0]) + 1 if zero.size else 0)
 
 
 # ----------------------------------------------------------------------------

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cstddef>
 
-#include "../../include/rqrcp.h"
+#include "rqrcp.h"
 
 namespace rq {
 

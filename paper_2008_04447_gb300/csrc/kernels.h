@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 
-#include "../../include/rqrcp.h"
+#include "rqrcp.h"
 
 namespace rq {
 
@@ -38,6 +38,9 @@ cudaError_t splitk_reduce_f32(const Ctx& c, int M, int N, int S, const float* P,
 bool tc_gemm_supported(const float* A, int lda, const float* B, int ldb);
 cudaError_t tc_gemm_tn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
                        int ldb, float beta, float* C, int ldc, bool transC, bool split3);
+// Same with A M-major (M x K column-major): C = alpha A B + beta C.
+cudaError_t tc_gemm_nn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
+                       int ldb, float beta, float* C, int ldc, bool split3);
 
 // Partial QRCP of the sample (l x nt): `steps` pivots, norms downdated.
 // Writes S11 (steps x steps, FP64, ld lds), swaps[steps], src[nt] (old position

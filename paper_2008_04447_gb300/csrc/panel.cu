@@ -2,8 +2,9 @@
 // the compact-WY factor T of Sec. 4.1 built alongside.
 //
 // One cooperative launch per panel.  CTA c keeps rows [c*rpc, (c+1)*rpc) of
-// the panel in shared memory (FP64, column-major inside the slab) for all b
-// reflectors.  Reflector j needs only global sums over the rows below j:
+// the panel in shared memory (storage precision, column-major inside the slab)
+// for all b reflectors.  The reflector scalars (norms, beta, tau) and T are
+// FP64; the dot products and updates run in the storage precision.  Reflector j needs only global sums over the rows below j:
 //   x2 = sum a_j^2, e'_c = sum a_j a_c (c > j), e_i = sum y_i a_j (i < j),
 // plus row j itself.  Each CTA writes its partial sums, one grid barrier
 // follows, and every CTA adds the partials in the same order, so all CTAs
@@ -24,6 +25,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxB = 256;
+constexpr int kMaxRec = 20;  // partial records summed per thread: G <= kMaxRec * kWarps = 160
 
 template <typename TS>
 struct PanelArgs {
@@ -49,19 +51,19 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
   const int bj = a.bj, rpc = a.rpc;
   const int r0 = cta * rpc;
   const int nr = max(0, min(rpc, a.mt - r0));
-  double* p = sm;                    // p[c * rpc + r]
-  double* tw = p + (size_t)bj * rpc; // bj
-  double* sums = tw + bj;            // bj
-  double* redw = sums + bj;          // kWarps * bj
-  double* Tm = redw + kWarps * bj;   // bj * bj (CTA 0)
-  double* tv = Tm + (size_t)bj * bj; // bj
-  double* tv2 = tv + bj;             // 2 * bj: row j of the panel, this step
+  double* tw = sm;                    // bj
+  double* sums = tw + bj;             // bj
+  double* redw = sums + bj;           // kWarps * bj
+  double* Tm = redw + kWarps * bj;    // bj * bj (CTA 0)
+  double* tv = Tm + (size_t)bj * bj;  // bj
+  double* tv2 = tv + bj;              // 2 * bj: row j of the panel, this step
+  TS* p = reinterpret_cast<TS*>(tv2 + 2 * bj);  // p[c * rpc + r]
   __shared__ double s_tau, s_y1, s_beta;
   const int recn = bj + 1;
 
   for (int e = tid; e < nr * bj; e += kThreads) {
     const int r = e % nr, c = e / nr;
-    p[(size_t)c * rpc + r] = static_cast<double>(a.P[(size_t)(r0 + r) + (size_t)c * a.ldp]);
+    p[(size_t)c * rpc + r] = a.P[(size_t)(r0 + r) + (size_t)c * a.ldp];
   }
   for (int e = tid; e < bj * bj; e += kThreads) Tm[e] = 0.0;
   __syncthreads();
@@ -72,11 +74,11 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
     double* rowb = a.rowbuf + (size_t)par * 2 * bj;
     // column j receives reflector j-1
     if (j > 0) {
-      const double t = tw[j];
+      const TS t = static_cast<TS>(tw[j]);
       for (int r = tid; r < nr; r += kThreads) {
         const int g = r0 + r;
         if (g >= j - 1) {
-          const double v = (g == j - 1) ? 1.0 : p[(size_t)(j - 1) * rpc + r];
+          const TS v = (g == j - 1) ? TS(1) : p[(size_t)(j - 1) * rpc + r];
           p[(size_t)j * rpc + r] = fma(-t, v, p[(size_t)j * rpc + r]);
         }
       }
@@ -85,27 +87,35 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
     // partial sums over rows g > j; columns c > j first receive reflector j-1
     for (int task = warp; task < bj; task += kWarps) {
       double acc = 0.0;
-      const double* aj = p + (size_t)j * rpc;
+      const TS* aj = p + (size_t)j * rpc;
       if (task == 0) {
+        // the squared norm feeds beta and tau: accumulated in FP64
         for (int r = lane; r < nr; r += 32)
-          if (r0 + r > j) acc = fma(aj[r], aj[r], acc);
+          if (r0 + r > j) {
+            const double x = static_cast<double>(aj[r]);
+            acc = fma(x, x, acc);
+          }
       } else if (task < bj - j) {
         const int c = j + task;
-        double* ac = p + (size_t)c * rpc;
-        const double t = (j > 0) ? tw[c] : 0.0;
+        TS* ac = p + (size_t)c * rpc;
+        const TS t = (j > 0) ? static_cast<TS>(tw[c]) : TS(0);
+        TS dot = TS(0);
         for (int r = lane; r < nr; r += 32) {
           const int g = r0 + r;
           if (j > 0 && g >= j - 1) {
-            const double v = (g == j - 1) ? 1.0 : p[(size_t)(j - 1) * rpc + r];
+            const TS v = (g == j - 1) ? TS(1) : p[(size_t)(j - 1) * rpc + r];
             ac[r] = fma(-t, v, ac[r]);
           }
-          if (g > j) acc = fma(aj[r], ac[r], acc);
+          if (g > j) dot = fma(aj[r], ac[r], dot);
         }
+        acc = static_cast<double>(dot);
       } else {
         const int i = task - (bj - j);
-        const double* yi = p + (size_t)i * rpc;
+        const TS* yi = p + (size_t)i * rpc;
+        TS dot = TS(0);
         for (int r = lane; r < nr; r += 32)
-          if (r0 + r > j) acc = fma(yi[r], aj[r], acc);
+          if (r0 + r > j) dot = fma(yi[r], aj[r], dot);
+        acc = static_cast<double>(dot);
       }
       acc = warp_sum(acc);
       if (lane == 0) part[(size_t)cta * recn + task] = acc;
@@ -114,16 +124,24 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
     if (r0 <= j && j < r0 + nr) {
       const int jl = j - r0;
       for (int c = tid; c < bj; c += kThreads) {
-        rowb[c] = (c >= j) ? p[(size_t)c * rpc + jl] : 0.0;
-        rowb[bj + c] = (c < j) ? p[(size_t)c * rpc + jl] : 0.0;
+        rowb[c] = (c >= j) ? static_cast<double>(p[(size_t)c * rpc + jl]) : 0.0;
+        rowb[bj + c] = (c < j) ? static_cast<double>(p[(size_t)c * rpc + jl]) : 0.0;
       }
     }
     if (!grid_barrier(a.bar, G, a.err)) return;
     // reduce the partials in a fixed order (CTA 0 also needs the e_i)
     const int need = (cta == 0) ? bj : (bj - j);
     for (int t = lane; t < need; t += 32) {
+      // independent loads first (all in flight together), then a fixed-order sum
+      double v[kMaxRec];
+#pragma unroll
+      for (int u = 0; u < kMaxRec; ++u) {
+        const int q = warp + u * kWarps;
+        v[u] = q < G ? __ldcg(part + (size_t)q * recn + t) : 0.0;
+      }
       double acc = 0.0;
-      for (int q = warp; q < G; q += kWarps) acc += __ldcg(part + (size_t)q * recn + t);
+#pragma unroll
+      for (int u = 0; u < kMaxRec; ++u) acc += v[u];
       redw[warp * bj + t] = acc;
     }
     __syncthreads();
@@ -157,8 +175,10 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
     for (int c = j + 1 + tid; c < bj; c += kThreads) tw[c] = tau * (tv2[c] + sums[c - j] / y1);
     for (int r = tid; r < nr; r += kThreads) {
       const int g = r0 + r;
-      if (g > j) p[(size_t)j * rpc + r] = tau != 0.0 ? p[(size_t)j * rpc + r] / y1 : 0.0;
-      else if (g == j) p[(size_t)j * rpc + r] = beta;
+      if (g > j)
+        p[(size_t)j * rpc + r] = tau != 0.0 ? static_cast<TS>(static_cast<double>(p[(size_t)j * rpc + r]) / y1) : TS(0);
+      else if (g == j)
+        p[(size_t)j * rpc + r] = static_cast<TS>(beta);
     }
     if (cta == 0) {
       // T(0:j, j) = -tau T(0:j, 0:j) (Y^T v_j)
@@ -177,17 +197,18 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
   for (int e = tid; e < nr * bj; e += kThreads) {
     const int r = e % nr, c = e / nr;
     const int g = r0 + r;
-    const double x = p[(size_t)c * rpc + r];
-    a.P[(size_t)g + (size_t)c * a.ldp] = static_cast<TS>(x);
-    a.Y[(size_t)g + (size_t)c * a.ldy] = static_cast<TS>(g < c ? 0.0 : (g == c ? 1.0 : x));
+    const TS x = p[(size_t)c * rpc + r];
+    a.P[(size_t)g + (size_t)c * a.ldp] = x;
+    a.Y[(size_t)g + (size_t)c * a.ldy] = g < c ? TS(0) : (g == c ? TS(1) : x);
   }
   if (cta == 0)
     for (int e = tid; e < bj * bj; e += kThreads) a.T[(size_t)(e / bj) * a.ldt + (e % bj)] = Tm[e];
 }
 
+template <typename TS>
 size_t smem_bytes(int bj, int rpc) {
-  return ((size_t)bj * rpc + bj + bj + (size_t)kWarps * bj + (size_t)bj * bj + 3 * (size_t)bj) *
-         sizeof(double);
+  return (bj + bj + (size_t)kWarps * bj + (size_t)bj * bj + 3 * (size_t)bj) * sizeof(double) +
+         (size_t)bj * rpc * sizeof(TS);
 }
 
 }  // namespace
@@ -202,9 +223,10 @@ cudaError_t panel_qr(const Ctx& c, TS* P, int ldp, int mt, int bj, TS* tau, TS* 
   if (bj > kMaxB || bj > mt || bj < 1) return cudaErrorInvalidValue;
   int G = (mt + 31) / 32;
   if (G > c.num_sms) G = c.num_sms;
+  if (G > kMaxRec * kWarps) G = kMaxRec * kWarps;
   if (G < 1) G = 1;
   const int rpc = (mt + G - 1) / G;
-  const size_t smem = smem_bytes(bj, rpc);
+  const size_t smem = smem_bytes<TS>(bj, rpc);
   static int max_optin = -1;
   if (max_optin < 0) {
     int dev = 0;

@@ -112,8 +112,10 @@ struct FactorWs {
   size_t bytes;
 };
 
-// Split-K partials of the b x n W^T product: up to 8 partial copies.
-inline size_t splitk_bytes_for(int b, int n, size_t elem) { return 8 * (size_t)b * n * elem; }
+inline int pad4(int x) { return (x + 3) / 4 * 4; }
+
+// Split-K partials of the b x n W^T product: up to 16 partial copies.
+inline size_t splitk_bytes_for(int b, int n, size_t elem) { return 16 * (size_t)b * n * elem; }
 
 template <typename TS>
 FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
@@ -127,8 +129,8 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
   w.Oh = c.take<double>((size_t)b * b);
   w.T = c.take<double>((size_t)b * b);
   w.Tts = c.take<TS>((size_t)b * b);
-  w.Ybuf = c.take<TS>((size_t)m * b);
-  w.YT = c.take<TS>((size_t)m * b);
+  w.Ybuf = c.take<TS>((size_t)pad4(m) * b);
+  w.YT = c.take<TS>((size_t)pad4(m) * b);
   w.Wt = c.take<TS>((size_t)b * n);
   w.ptmp = c.take<TS>((size_t)2 * b * m);
   w.jtmp = c.take<int>((size_t)2 * b);
@@ -163,6 +165,31 @@ int ensure_ws(rq_handle h, size_t bytes) {
   return RQ_OK;
 }
 
+// C (bj x n2, ld ldc) = P^T Q with P (K x bj) and Q (K x n2) column-major: the
+// skinny products W^T = (Y T)^T A2 and Y2^T A.  FP32 runs on the tensor cores
+// (3xTF32, computed as (Q^T P)^T); FP64 and unaligned operands use the SIMT kernel.
+template <typename TS>
+cudaError_t prod_tn_skinny(const Ctx& c, int bj, int n2, int K, const TS* P, int ldp, const TS* Q, int ldq, TS* C,
+                           int ldc) {
+  if constexpr (sizeof(TS) == sizeof(float)) {
+    if (tc_gemm_supported(Q, ldq, P, ldp))
+      return tc_gemm_tn(c, n2, bj, K, 1.f, Q, ldq, P, ldp, 0.f, C, ldc, true, true);
+  }
+  return gemm<TS>(c, true, false, bj, n2, K, TS(1), P, ldp, Q, ldq, TS(0), C, ldc);
+}
+
+// C (M x N) = alpha A B + beta C, A M x K and B K x N column-major: the block
+// update A2 -= Y W^T, the sketch Omega A and Z1 = A V.  FP32 on the tensor cores
+// (3xTF32), else SIMT.
+template <typename TS>
+cudaError_t prod_nn(const Ctx& c, int M, int N, int K, TS alpha, const TS* A, int lda, const TS* B, int ldb, TS beta,
+                    TS* C, int ldc) {
+  if constexpr (sizeof(TS) == sizeof(float)) {
+    if (tc_gemm_supported(A, lda, B, ldb)) return tc_gemm_nn(c, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, true);
+  }
+  return gemm<TS>(c, false, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 // Blocked Householder QR, pivoted by the sample (Alg. 4) or unpivoted.
 template <typename TS>
 int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega,
@@ -182,9 +209,10 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
   if (pivot) {
     // Alg. 4: B = Omega A
     Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * l * (double)m * n, sz * ((double)m * n + (double)l * m + (double)l * n));
-    e = gemm<TS>(c, false, false, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l);
+    e = prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l);
     if (e != cudaSuccess) return cuda_fail(h, e, "sketch");
   }
+  const int ldy = pad4(m);
   for (int j0 = 0; j0 < k; j0 += b) {
     const int bj = (k - j0) < b ? (k - j0) : b;
     const int nt = n - j0, mt = m - j0, n2 = nt - bj;
@@ -201,7 +229,7 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
     }
     {
       Phase ph(h, st, RQ_PHASE_PANEL, 2.0 * (double)mt * bj * bj, 2.0 * sz * (double)mt * bj);
-      e = panel_qr<TS>(c, Aj, lda, mt, bj, tau + j0, w.Ybuf, mt, w.T, b, w.pscr);
+      e = panel_qr<TS>(c, Aj, lda, mt, bj, tau + j0, w.Ybuf, ldy, w.T, b, w.pscr);
       if (e != cudaSuccess) return cuda_fail(h, e, "panel");
     }
     if (n2 > 0) {
@@ -219,10 +247,9 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
         // W^T = (Y T)^T A2 ; A2 -= Y W^T  (block reflector, Alg. 4 "finish b rows", "update")
         Phase ph(h, st, RQ_PHASE_TRAILING, 4.0 * mt * (double)n2 * bj + 2.0 * mt * (double)bj * bj,
                  sz * (3.0 * mt * (double)n2 + 2.0 * bj * (double)n2 + 3.0 * mt * (double)bj));
-        e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, mt, Tm, b, TS(0), w.YT, mt);
-        if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, n2, mt, TS(1), w.YT, mt, A2, lda, TS(0), w.Wt, b);
-        if (e == cudaSuccess)
-          e = gemm<TS>(c, false, false, mt, n2, bj, TS(-1), w.Ybuf, mt, w.Wt, b, TS(1), A2, lda);
+        e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, ldy, Tm, b, TS(0), w.YT, ldy);
+        if (e == cudaSuccess) e = prod_tn_skinny<TS>(c, bj, n2, mt, w.YT, ldy, A2, lda, w.Wt, b);
+        if (e == cudaSuccess) e = prod_nn<TS>(c, mt, n2, bj, TS(-1), w.Ybuf, ldy, w.Wt, b, TS(1), A2, lda);
         if (e != cudaSuccess) return cuda_fail(h, e, "trailing update");
       }
       if (pivot && j0 + bj < k) {
@@ -300,7 +327,7 @@ cudaError_t sketch_gemm(const Ctx& c, bool mixed, int l, int n, int m, const TS*
   if constexpr (sizeof(TS) == sizeof(float)) {
     if (mixed) return gemm_bf16_inputs(c, l, n, m, Omega, ldo, A, lda, B, l);
   }
-  return gemm<TS>(c, false, false, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), B, l);
+  return prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), B, l);
 }
 
 template <typename TS>
@@ -366,7 +393,7 @@ int run_trqrcp(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, in
                2.0 * bj * (double)mt * n + 2.0 * bj * (double)mt * j0 + 2.0 * bj * (double)j0 * n +
                    2.0 * bj * (double)bj * n,
                sz * ((double)mt * n + (double)mt * (bj + j0) + (double)(j0 + 2 * bj) * n));
-      e = gemm<TS>(c, true, false, bj, n, mt, TS(1), Y2, ldy, A + j0, lda, TS(0), w.X, b);
+      e = prod_tn_skinny<TS>(c, bj, n, mt, Y2, ldy, A + j0, lda, w.X, b);
       if (e == cudaSuccess && j0 > 0) {
         e = gemm<TS>(c, true, false, bj, j0, mt, TS(1), Y2, ldy, Y + j0, ldy, TS(0), w.G, b);
         if (e == cudaSuccess) e = gemm<TS>(c, false, false, bj, n, j0, TS(-1), w.G, b, w.Wt, k, TS(1), w.X, b);
@@ -531,7 +558,7 @@ int run_tuxv(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, int 
   {
     // Z1 = A V(:, 1:k): one more pass over A (Alg. 6)
     Phase ph(h, st, RQ_PHASE_TRAILING, 2.0 * m * (double)n * k, sz * ((double)m * n + (double)n * k + (double)m * k));
-    e = gemm<TS>(c, false, false, m, k, n, TS(1), A, lda, V, ldv, TS(0), w.Z1, m);
+    e = prod_nn<TS>(c, m, k, n, TS(1), A, lda, V, ldv, TS(0), w.Z1, m);
     if (e != cudaSuccess) return cuda_fail(h, e, "Z1 = A V");
   }
   {

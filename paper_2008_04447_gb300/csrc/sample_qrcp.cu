@@ -1,19 +1,22 @@
 // Partial QRCP of the sample matrix B (Sec. 3.2; Alg. 4, "get b column pivots").
 //
 // One cooperative launch per block of pivots.  Each CTA holds a slab of the
-// sample's columns in shared memory (FP64, row-major inside the slab so that
-// consecutive threads touch consecutive columns) for all `steps` decisions,
+// sample's columns in shared memory (in the storage precision, row-major inside
+// the slab so that consecutive threads touch consecutive columns) for all
+// `steps` decisions,
 // so B is read from HBM once and written once per block.  Per decision:
 //   1. every CTA finds its best alive column (max downdated squared norm,
 //      ties -> lowest current position) and publishes (norm^2, position,
 //      column values) to a double-buffered candidate table;
 //   2. one grid barrier;
 //   3. every CTA reduces the table in the same order (so all agree bit for
-//      bit), rebuilds the Householder vector of the winner in FP64, applies it
-//      to its alive columns and downdates their norms (removing the
+//      bit), rebuilds the Householder vector of the winner in FP64 (tau from
+//      the vector as stored), applies it to its alive columns in the storage
+//      precision and downdates their FP64 squared norms (removing the
 //      contribution of the finished row, Alg. 1), recomputing a norm from
 //      the remaining rows when the downdated value has fallen to sqrt(eps)
-//      of its last exactly computed value.
+//      of its last exactly computed value (eps of the sample's precision:
+//      the downdate's relative error is about eps / (that ratio)).
 // Column exchanges are never moved in memory: each CTA tracks the current
 // position of its columns (only the column at position i moves per swap), so
 // ties resolve exactly as with physical swaps.
@@ -29,6 +32,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSteps = 256;
+constexpr int kMaxRecS = 8;  // candidate records per lane: G <= 256
 
 template <typename TS>
 struct SqArgs {
@@ -55,12 +59,14 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
   const int l = a.l, cpc = a.cpc, steps = a.steps;
   const int c0 = cta * cpc;
   const int nc = max(0, min(cpc, a.nt - c0));
-  const double tol = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
-  double* s = sm;                             // s[r * cpc + c]
-  double* nu2 = s + (size_t)l * cpc;
-  double* ref2 = nu2 + cpc;
-  double* vv = ref2 + cpc;  // l
-  int* pos = reinterpret_cast<int*>(vv + l);
+  // recompute a downdated norm once it has fallen to sqrt(eps) of its last exact
+  // value, eps being the precision the sample is held in
+  const double tol = sizeof(TS) == sizeof(double) ? 1.4901161193847656e-08 : 3.4526698300124393e-04;
+  double* nu2 = sm;                           // cpc
+  double* ref2 = nu2 + cpc;                   // cpc
+  TS* s = reinterpret_cast<TS*>(ref2 + cpc);  // s[r * cpc + c]
+  TS* vv = s + (size_t)l * cpc;               // l
+  int* pos = reinterpret_cast<int*>(vv + l + 1);
   int* alive = pos + cpc;
   __shared__ double red_v[kWarps];
   __shared__ int red_p[kWarps], red_t[kWarps];
@@ -71,13 +77,13 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
 
   for (int e = tid; e < l * nc; e += kThreads) {
     const int r = e % l, c = e / l;
-    s[(size_t)r * cpc + c] = static_cast<double>(a.B[(size_t)(c0 + c) * a.ldb + r]);
+    s[(size_t)r * cpc + c] = a.B[(size_t)(c0 + c) * a.ldb + r];
   }
   __syncthreads();
   for (int c = tid; c < nc; c += kThreads) {
     double acc = 0.0;
     for (int r = 0; r < l; ++r) {
-      const double x = s[(size_t)r * cpc + c];
+      const double x = static_cast<double>(s[(size_t)r * cpc + c]);
       acc = fma(x, x, acc);
     }
     nu2[c] = acc;
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     {
       const int lc = s_best_lc;
       if (lc >= 0)
-        for (int r = tid; r < l; r += kThreads) tab[(size_t)cta * rec + 2 + r] = s[(size_t)r * cpc + lc];
+        for (int r = tid; r < l; r += kThreads) tab[(size_t)cta * rec + 2 + r] = static_cast<double>(s[(size_t)r * cpc + lc]);
     }
     // (2)
     if (!grid_barrier(a.bar, G, a.err)) return;
@@ -121,17 +127,26 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     if (warp == 0) {
       double gv = -1.0;
       int gp = -1, gt = -1;
-      for (int q = lane; q < G; q += 32) {
-        const double v = __ldcg(tab + (size_t)q * rec + 0);
-        const int p = static_cast<int>(__ldcg(tab + (size_t)q * rec + 1));
-        if (better(v, p, gv, gp)) { gv = v; gp = p; gt = q; }
+      double vs[kMaxRecS], ps[kMaxRecS];
+#pragma unroll
+      for (int u = 0; u < kMaxRecS; ++u) {
+        const int q = lane + 32 * u;
+        vs[u] = q < G ? __ldcg(tab + (size_t)q * rec + 0) : -1.0;
+        ps[u] = q < G ? __ldcg(tab + (size_t)q * rec + 1) : -1.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kMaxRecS; ++u) {
+        const int q = lane + 32 * u;
+        const int p = static_cast<int>(ps[u]);
+        if (q < G && better(vs[u], p, gv, gp)) { gv = vs[u]; gp = p; gt = q; }
       }
       warp_argmax(gv, gp, gt);
       if (lane == 0) { s_win_cta = gt; s_win_pos = gp; }
     }
     __syncthreads();
     const int wc = s_win_cta, q = s_win_pos;
-    for (int r = tid; r < l; r += kThreads) vv[r] = __ldcg(tab + (size_t)wc * rec + 2 + r);
+    __shared__ double wcol[kMaxSteps + 128];
+    for (int r = tid; r < l; r += kThreads) wcol[r] = __ldcg(tab + (size_t)wc * rec + 2 + r);
     if (tid == 0) {
       if (wc == cta) { alive[s_best_lc] = 0; pos[s_best_lc] = i; }
       if (cta == 0) { a.swaps[i] = q; s_swaps[i] = q; }
@@ -142,9 +157,9 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     // reflector of the winner, rows i..l-1 (Sec. 2 formula, v_i = 1)
     if (warp == 0) {
       double x2 = 0.0;
-      for (int r = i + 1 + lane; r < l; r += 32) x2 = fma(vv[r], vv[r], x2);
+      for (int r = i + 1 + lane; r < l; r += 32) x2 = fma(wcol[r], wcol[r], x2);
       x2 = warp_sum(x2);
-      const double alpha = vv[i];
+      const double alpha = wcol[i];
       const double nrm2 = fma(alpha, alpha, x2);
       double beta = 0.0, y1 = 1.0;
       const bool zero = !(nrm2 > 0.0);
@@ -155,38 +170,38 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
       }
       if (cta == 0) {
         double* col = a.S11 + (size_t)i * a.lds;
-        for (int r = lane; r < steps; r += 32) col[r] = r < i ? vv[r] : (r == i ? beta : 0.0);
+        for (int r = lane; r < steps; r += 32) col[r] = r < i ? wcol[r] : (r == i ? beta : 0.0);
       }
       __syncwarp();
       double v2 = 0.0;
       for (int r = lane; r < l; r += 32) {
-        double v;
-        if (r < i) v = 0.0;
-        else if (r == i) v = 1.0;
-        else v = zero ? 0.0 : vv[r] / y1;
+        TS v;
+        if (r < i) v = TS(0);
+        else if (r == i) v = TS(1);
+        else v = zero ? TS(0) : static_cast<TS>(wcol[r] / y1);
         vv[r] = v;
-        if (r > i) v2 = fma(v, v, v2);
+        if (r > i) v2 = fma(static_cast<double>(v), static_cast<double>(v), v2);
       }
       v2 = warp_sum(v2);
       if (lane == 0) s_tau = zero ? 0.0 : 2.0 / (1.0 + v2);
     }
     __syncthreads();
-    const double tau = s_tau;
+    const TS tau = static_cast<TS>(s_tau);
     for (int c = tid; c < nc; c += kThreads) {
       if (!alive[c]) continue;
-      if (tau != 0.0) {
-        double w = s[(size_t)i * cpc + c];
+      if (tau != TS(0)) {
+        TS w = s[(size_t)i * cpc + c];
         for (int r = i + 1; r < l; ++r) w = fma(vv[r], s[(size_t)r * cpc + c], w);
-        const double tw = tau * w;
+        const TS tw = tau * w;
         s[(size_t)i * cpc + c] -= tw;
         for (int r = i + 1; r < l; ++r) s[(size_t)r * cpc + c] = fma(-tw, vv[r], s[(size_t)r * cpc + c]);
       }
-      const double x = s[(size_t)i * cpc + c];
+      const double x = static_cast<double>(s[(size_t)i * cpc + c]);
       double nn = nu2[c] - x * x;
       if (nn <= tol * ref2[c]) {
         nn = 0.0;
         for (int r = i + 1; r < l; ++r) {
-          const double y = s[(size_t)r * cpc + c];
+          const double y = static_cast<double>(s[(size_t)r * cpc + c]);
           nn = fma(y, y, nn);
         }
         ref2[c] = nn;
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
   for (int c = tid; c < nc; c += kThreads) a.src[pos[c]] = c0 + c;
   for (int e = tid; e < l * nc; e += kThreads) {
     const int r = e % l, c = e / l;
-    if (alive[c]) a.Bn[(size_t)(pos[c] - steps) * a.ldbn + r] = static_cast<TS>(s[(size_t)r * cpc + c]);
+    if (alive[c]) a.Bn[(size_t)(pos[c] - steps) * a.ldbn + r] = s[(size_t)r * cpc + c];
   }
   if (cta == 0) {
     for (int i = tid; i < steps; i += kThreads) {
@@ -215,7 +230,8 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
 
 template <typename TS>
 size_t smem_bytes(int l, int cpc) {
-  return ((size_t)l * cpc + 2 * (size_t)cpc + l) * sizeof(double) + 2 * (size_t)cpc * sizeof(int);
+  return 2 * (size_t)cpc * sizeof(double) + ((size_t)l * cpc + l + 1) * sizeof(TS) + 2 * (size_t)cpc * sizeof(int) +
+         16;
 }
 
 }  // namespace
@@ -226,9 +242,10 @@ template <typename TS>
 cudaError_t sample_qrcp(const Ctx& c, const TS* B, int ldb, int l, int nt, int steps, TS* Bn,
                         int ldbn, double* S11, int lds, int* swaps, int* src, int* chg,
                         double* cand) {
-  if (steps > kMaxSteps || steps > nt || steps > l) return cudaErrorInvalidValue;
+  if (steps > kMaxSteps || steps > nt || steps > l || l > kMaxSteps + 128) return cudaErrorInvalidValue;
   int G = (nt + 31) / 32;
   if (G > c.num_sms) G = c.num_sms;
+  if (G > 32 * kMaxRecS) G = 32 * kMaxRecS;
   if (G < 1) G = 1;
   int cpc = (nt + G - 1) / G;
   size_t smem = smem_bytes<TS>(l, cpc);

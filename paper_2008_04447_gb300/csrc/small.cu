@@ -56,21 +56,24 @@ __global__ void omegahat_kernel(const double* __restrict__ S11, int lds, const T
   }
 }
 
-// B1 -= Oh * R12 (K = bj), one thread per output entry, FP64 accumulation.
+// B1 -= Oh * R12 (K = bj), one thread per output entry.  Omegahat_11 comes
+// from an FP64 solve; the product accumulates in the storage precision.
 template <typename TS>
 __global__ void sample_update_kernel(int bj, int n2, const double* __restrict__ Oh, int ldo,
                                      const TS* __restrict__ R12, int ldr, TS* __restrict__ B1, int ldb) {
-  extern __shared__ double sO[];  // bj x bj
-  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) sO[e] = Oh[(e % bj) + (size_t)(e / bj) * ldo];
+  extern __shared__ __align__(8) unsigned char so_raw[];
+  TS* sO = reinterpret_cast<TS*>(so_raw);  // bj x bj
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x)
+    sO[e] = static_cast<TS>(Oh[(e % bj) + (size_t)(e / bj) * ldo]);
   __syncthreads();
   const int col = blockIdx.x;
   if (col >= n2) return;
   const TS* rc = R12 + (size_t)col * ldr;
   TS* bc = B1 + (size_t)col * ldb;
   for (int r = threadIdx.x; r < bj; r += blockDim.x) {
-    double acc = 0.0;
-    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], static_cast<double>(rc[i]), acc);
-    bc[r] = static_cast<TS>(static_cast<double>(bc[r]) - acc);
+    TS acc = TS(0);
+    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], rc[i], acc);
+    bc[r] -= acc;
   }
 }
 
@@ -118,22 +121,24 @@ __global__ void trq_fix_rows(TS* __restrict__ Zb, int ldz, int bj, int j0, const
   }
 }
 
-// B1(:, t) -= Oh * Z(:, idx[t]) (K = bj), FP64 accumulation.
+// B1(:, t) -= Oh * Z(:, idx[t]) (K = bj), storage-precision accumulation.
 template <typename TS>
 __global__ void sample_update_idx_kernel(int bj, int n2, const double* __restrict__ Oh, int ldo,
                                          const TS* __restrict__ Zb, int ldz, const int* __restrict__ idx,
                                          TS* __restrict__ B1, int ldb) {
-  extern __shared__ double sO[];
-  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) sO[e] = Oh[(e % bj) + (size_t)(e / bj) * ldo];
+  extern __shared__ __align__(8) unsigned char so_raw[];
+  TS* sO = reinterpret_cast<TS*>(so_raw);
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x)
+    sO[e] = static_cast<TS>(Oh[(e % bj) + (size_t)(e / bj) * ldo]);
   __syncthreads();
   const int col = blockIdx.x;
   if (col >= n2) return;
   const TS* rc = Zb + (size_t)idx[col] * ldz;
   TS* bc = B1 + (size_t)col * ldb;
   for (int r = threadIdx.x; r < bj; r += blockDim.x) {
-    double acc = 0.0;
-    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], static_cast<double>(rc[i]), acc);
-    bc[r] = static_cast<TS>(static_cast<double>(bc[r]) - acc);
+    TS acc = TS(0);
+    for (int i = r; i < bj; ++i) acc = fma(sO[r + i * bj], rc[i], acc);
+    bc[r] -= acc;
   }
 }
 

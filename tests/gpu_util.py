@@ -21,10 +21,18 @@ def to_host(t):
     return t.detach().cpu().double().numpy()
 
 
-def first_near_tie(gaps_per_block, b, thr):
-    """Global pivot index of the first decision whose relative gap is below thr."""
+def first_near_tie(gaps_per_block, b, thr, sample_norms=None):
+    """Global pivot index of the first decision whose relative gap is below thr.
+
+    With sample_norms, the threshold of block J grows by ||B^[0]|| / ||B^[J]||:
+    the update formula cancels entries of the first sample's size, so a sample
+    held in precision u is accurate to about u ||B^[0]|| / ||B^[J]|| relative.
+    """
     for J, g in enumerate(gaps_per_block):
-        idx = np.nonzero(np.asarray(g) < thr)[0]
+        t = thr
+        if sample_norms is not None and sample_norms[J] > 0:
+            t = thr * sample_norms[0] / sample_norms[J]
+        idx = np.nonzero(np.asarray(g) < t)[0]
         if idx.size:
             return J * b + int(idx[0])
     return None
