@@ -23,6 +23,10 @@ constexpr int NT = 256;
 constexpr int NW = NT / 32;
 constexpr int kMaxBB = 64;   // largest block size of the batched path
 constexpr int kMaxLB = 128;  // largest sample rank of the batched path
+// Dynamic shared memory per CTA: the block GEMM's tiles, or (at other times)
+// the live sample or the current panel when they fit, so that the serial
+// pivot / reflector steps run out of shared memory instead of L2.
+constexpr int kStageFloats = 50 * 1024;  // 200 KB
 
 __device__ __forceinline__ float bsum_f(float v, float* red) {
   v = warp_sum(v);
@@ -207,21 +211,24 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
     const double tu = s.sc[0], y1 = s.sc[1];
     for (int g = j + 1 + tid; g < mt; g += NT) aj[g] = tu != 0.0 ? (float)((double)aj[g] / y1) : 0.f;
     __syncthreads();
-    // d_c = sum_{g > j} v_g P(g, c) for every other column c of the panel
-    float d[kMaxBB];
+    // d_c = sum_{g > j} v_g P(g, c) for every other column c of the panel,
+    // sixteen columns at a time
+    for (int cb = 0; cb < bj; cb += 16) {
+      float d[16];
 #pragma unroll
-    for (int c = 0; c < kMaxBB; ++c) d[c] = 0.f;
-    for (int g = j + 1 + tid; g < mt; g += NT) {
-      const float v = aj[g];
+      for (int c = 0; c < 16; ++c) d[c] = 0.f;
+      for (int g = j + 1 + tid; g < mt; g += NT) {
+        const float v = aj[g];
 #pragma unroll
-      for (int c = 0; c < kMaxBB; ++c)
-        if (c < bj && c != j) d[c] = fmaf(v, P[g + (size_t)c * ldp], d[c]);
-    }
+        for (int c = 0; c < 16; ++c)
+          if (cb + c < bj && cb + c != j) d[c] = fmaf(v, P[g + (size_t)(cb + c) * ldp], d[c]);
+      }
 #pragma unroll
-    for (int c = 0; c < kMaxBB; ++c) {
-      if (c >= bj) break;
-      const float t = warp_sum(d[c]);
-      if (lane == 0) s.dots[warp][c] = t;
+      for (int c = 0; c < 16; ++c) {
+        if (cb + c >= bj) break;
+        const float t = warp_sum(d[c]);
+        if (lane == 0) s.dots[warp][cb + c] = t;
+      }
     }
     __syncthreads();
     if (tid < bj) {
@@ -403,6 +410,38 @@ __device__ void copy_T(const double* T, int ldt, int bj, float* Tf, int ldf) {
   __syncthreads();
 }
 
+__device__ void copy_mat(const float* src, int lds, int rows, int cols, float* dst, int ldd) {
+  for (int e = threadIdx.x; e < rows * cols; e += NT) {
+    const int i = e % rows, j = e / rows;
+    dst[i + (size_t)j * ldd] = src[i + (size_t)j * lds];
+  }
+  __syncthreads();
+}
+
+// Panel factorisation, staged through shared memory when the panel fits.
+__device__ void panel_staged(float* P, int ldp, int mt, int bj, float* Yout, int ldy, float* tau, double* T, int ldt,
+                             Shm& s, float* sm) {
+  if ((size_t)mt * bj <= (size_t)kStageFloats) {
+    copy_mat(P, ldp, mt, bj, sm, mt);
+    panel_b(sm, mt, mt, bj, Yout, ldy, tau, T, ldt, s);
+    copy_mat(sm, mt, mt, bj, P, ldp);
+  } else {
+    panel_b(P, ldp, mt, bj, Yout, ldy, tau, T, ldt, s);
+  }
+}
+
+// Sample QRCP, staged through shared memory when the live sample fits.
+__device__ void sample_staged(float* B, int l, int nt, int steps, int* jp, double* nu2, double* ref2, double* S11,
+                              int lds, Shm& s, float* sm) {
+  if ((size_t)l * nt <= (size_t)kStageFloats) {
+    copy_mat(B, l, l, nt, sm, l);
+    sample_qrcp_b(sm, l, nt, steps, jp, nu2, ref2, S11, lds, s);
+    copy_mat(sm, l, l, nt, B, l);
+  } else {
+    sample_qrcp_b(B, l, nt, steps, jp, nu2, ref2, S11, lds, s);
+  }
+}
+
 // QR of the rows x k matrix M in place (block size b) with explicit Q(:, 1:k)
 // into Q (ld ldq) and, if Rout, R (k x k, upper) into Rout.
 __device__ void qr_explicit_b(float* M, int ldm, int rows, int k, int b, Slot& w, float* Q, int ldq, float* Rout,
@@ -414,7 +453,7 @@ __device__ void qr_explicit_b(float* M, int ldm, int rows, int k, int b, Slot& w
     const int j0 = J * b, bj = min(b, k - j0), mt = rows - j0, n2 = k - j0 - bj;
     float* Yj = w.Yq + j0 + (size_t)j0 * rows;
     double* Tj = w.Tq + (size_t)J * b * b;
-    panel_b(M + j0 + (size_t)j0 * ldm, ldm, mt, bj, Yj, rows, w.tauq + j0, Tj, b, s);
+    panel_staged(M + j0 + (size_t)j0 * ldm, ldm, mt, bj, Yj, rows, w.tauq + j0, Tj, b, s, sm);
     if (n2 > 0) {
       copy_T(Tj, b, bj, w.Tf, b);
       float* M2 = M + j0 + (size_t)(j0 + bj) * ldm;
@@ -471,7 +510,7 @@ __device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool
   for (int j0 = 0; j0 < k; j0 += b) {
     const int bj = min(b, k - j0), nt = n - j0, mt = m - j0, n2 = nt - bj;
     float* BJ = w.B + (size_t)j0 * l;  // the live sample: columns j0.. (exchanged in place)
-    sample_qrcp_b(BJ, l, nt, bj, w.jp + j0, w.nu2 + j0, w.ref2 + j0, w.S11, b, s);
+    sample_staged(BJ, l, nt, bj, w.jp + j0, w.nu2 + j0, w.ref2 + j0, w.S11, b, s, sm);
     // selected columns of A - Y W^T
     for (int e = tid; e < m * bj; e += NT) {
       const int g = e % m, c = e / m;
@@ -485,7 +524,7 @@ __device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool
     __syncthreads();
     if (j0 > 0) gemm_b<false, false>(m, bj, j0, -1.f, w.Y, m, w.Wsel, k, 1.f, w.P, m, sm);
     float* Y2 = w.Y + j0 + (size_t)j0 * m;
-    panel_b(w.P + j0, m, mt, bj, Y2, m, w.taus + j0, w.T, b, s);
+    panel_staged(w.P + j0, m, mt, bj, Y2, m, w.taus + j0, w.T, b, s, sm);
     copy_T(w.T, b, bj, w.Tf, b);
     // W_2^T = T_2^T (Y_2^T A - (Y_2^T Y_1) W_1^T)
     gemm_b<true, false>(bj, n, mt, 1.f, Y2, m, A + j0, lda, 0.f, w.Xt, b, sm);
@@ -579,7 +618,8 @@ size_t batched_slot_bytes(int max_m, int max_n, int max_k, int max_b, int max_p)
 
 int batched_limits_ok(int max_b, int max_p) { return max_b >= 1 && max_b <= kMaxBB && max_b + max_p <= kMaxLB; }
 
-constexpr size_t kBatchSmem = 2 * 32 * (128 + 32 + 2) * sizeof(float);
+constexpr size_t kBatchSmem = (size_t)kStageFloats * sizeof(float);
+static_assert(kStageFloats >= 2 * 32 * (128 + 32 + 2), "the GEMM tiles share the staging area");
 
 cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
                          int* counter, bool mixed) {

@@ -257,7 +257,16 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
         Phase ph(h, st, RQ_PHASE_SAMPLE_UPDATE, (double)bj * bj * bj / 3.0 + (double)bj * bj * n2,
                  sz * 3.0 * bj * (double)n2);
         e = omegahat11<TS>(c, w.S11, b, Aj, lda, bj, w.Oh, b);
-        if (e == cudaSuccess) e = sample_update<TS>(c, bj, n2, w.Oh, b, A2, lda, Bn, l);
+        // B1 -= Omegahat11 R12 with R12 the top bj rows of the updated A2
+        if (e == cudaSuccess) {
+          if constexpr (sizeof(TS) == sizeof(double)) {
+            e = gemm<TS>(c, false, false, bj, n2, bj, TS(-1), reinterpret_cast<const TS*>(w.Oh), b, A2, lda, TS(1),
+                         Bn, l);
+          } else {
+            e = convert<TS, double>(c, bj, bj, w.Oh, b, w.Tts, b);
+            if (e == cudaSuccess) e = prod_nn<TS>(c, bj, n2, bj, TS(-1), w.Tts, b, A2, lda, TS(1), Bn, l);
+          }
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "sample update");
       }
     }

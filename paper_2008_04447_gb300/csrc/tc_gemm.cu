@@ -428,7 +428,9 @@ cudaError_t tc_gemm_any(const Ctx& c, bool amn, int M, int N, int K, float alpha
                         const float* B, int ldb, float beta, float* C, int ldc, bool transC, bool split3) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (!tc_gemm_supported(A, lda, B, ldb)) return cudaErrorNotSupported;
-  const int bn = N <= 64 ? 64 : 128;
+  // 64-column tiles when N is small or K is short (two CTAs per SM, so one
+  // CTA's epilogue overlaps the other's loads); 128 otherwise
+  const int bn = (N <= 64 || K <= 64) ? 64 : 128;
   CUtensorMap ma, mb;
   const bool okA = amn ? make_map_mn(&ma, A, M, K, lda) : make_map(&ma, A, K, M, lda, TBM);
   if (!okA || !make_map(&mb, B, K, N, ldb, bn)) return cudaErrorInvalidValue;
