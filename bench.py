@@ -8,7 +8,9 @@ time ratio).  Inputs are 2.1 GB, larger than L2.
 
 Extra legs (rank 0): unpivoted blocked QR of the same matrix, the FP32 path,
 an end-to-end number with host buffers, per-phase timing with CUDA events,
-the CPU oracle on a bounded sample.  ``--impl reference`` times the CPU
+repeated sampling (RSRQRCP) against the update formula on the same matrix,
+the CPU oracle on a bounded sample, truncated TUXV of a 32768 x 16384 matrix,
+the batched TUXV of 4096 small problems and the Poisson serving sweep.  ``--impl reference`` times the CPU
 oracle alone.  Under torchrun every rank factorises its own matrix (replicas).
 """
 from __future__ import annotations
@@ -41,7 +43,7 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--decades", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg but the timed RQRCP")
-    ap.add_argument("--legs", default="qr,e2e,fp32,cpu,tuxv,batched,serving",
+    ap.add_argument("--legs", default="qr,e2e,fp32,rsrqrcp,cpu,tuxv,batched,serving",
                     help="extra legs to run (comma list); --no-extras clears it")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the timed RQRCP")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
@@ -167,6 +169,49 @@ def to_device_f32(host):
     from paper_2008_04447_gb300 import colmajor
     return [(colmajor(torch.as_tensor(a, dtype=torch.float32)).cuda(),
              colmajor(torch.as_tensor(om, dtype=torch.float32)).cuda(), b, p, k) for a, om, b, p, k in host]
+
+
+def leg_rsrqrcp(h, A0, A, Om, b, p, fl, rqrcp_ms, prec):
+    """RSRQRCP (fresh Gaussian per block, Sec. 3.4) against RQRCP with the update
+    formula on the same matrix: FP64 (one timed step) and FP32 (three)."""
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    m, n = A0.shape
+    l = b + p
+    ex = sum(2.0 * l * (m - j0 - b) * (n - j0 - b) for j0 in range(0, min(m, n) - b, b))
+    out = {"extra_sketch_flops": ex}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def rs(W, src):
+        W.copy_(src)
+        h.rsrqrcp(W, 1234, b, p)
+    ms = timed(lambda: rs(A, A0), 1)
+    out[prec] = {"rsrqrcp_s": ms / 1e3, "rqrcp_s": rqrcp_ms / 1e3, "rsrqrcp_over_rqrcp": ms / rqrcp_ms,
+                 "tflops_counting_4n3_3": fl / (ms / 1e3) / 1e12}
+    if prec == "fp64":
+        A32 = colmajor(A0.float())
+        Om32 = colmajor(Om.float())
+        W = torch.empty_like(A32)
+
+        def up(W, src):
+            W.copy_(src)
+            h.rqrcp(W, Om32, b, p)
+        r32 = timed(lambda: up(W, A32), 3)
+        s32 = timed(lambda: rs(W, A32), 3)
+        out["fp32"] = {"rsrqrcp_s": s32 / 1e3, "rqrcp_s": r32 / 1e3, "rsrqrcp_over_rqrcp": s32 / r32}
+        del A32, W
+    return out
 
 
 def leg_tuxv(h, steps=3, warmup=3):
@@ -478,6 +523,11 @@ def main():
         line["fp32"] = {"rqrcp_s": r32 / 1e3, "rqrcp_tflops": fl / (r32 / 1e3) / 1e12, "qr_s": q32 / 1e3,
                         "qr_tflops": fl / (q32 / 1e3) / 1e12, "rqrcp_over_qr": r32 / q32}
         del A32, W
+
+    if "rsrqrcp" in legs:
+        # ablation of the sample update (Sec. 3.4): repeated sampling re-sketches the
+        # trailing matrix with fresh device draws at every block; same matrix
+        line["rsrqrcp"] = leg_rsrqrcp(h, A0, A, Om, b, p, fl, ms_step, args.prec)
 
     if "cpu" in legs:
         line["cpu_baseline"] = cpu_baseline(args.cpu_n, b, p, args.decades)

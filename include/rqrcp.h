@@ -51,6 +51,7 @@ extern "C" {
 #define RQ_OP_TRQRCP 1
 #define RQ_OP_TUXV 2
 #define RQ_OP_QR 3
+#define RQ_OP_RSRQRCP 4
 
 typedef struct rq_handle_s* rq_handle;
 typedef void* rq_stream; /* cudaStream_t */
@@ -81,7 +82,7 @@ int rq_last_error(rq_handle h, char* buf, size_t len);
 long long rq_launch_count(rq_handle h);
 
 /* Phases of the factorisations, for per-phase timing. */
-#define RQ_PHASE_SKETCH 0        /* B = Omega A (Alg. 4 line "form the initial sample") */
+#define RQ_PHASE_SKETCH 0        /* B = Omega A, the initial sample (Alg. 4) */
 #define RQ_PHASE_SAMPLE_QRCP 1   /* block pivots from the sample (Sec. 3.2) */
 #define RQ_PHASE_PERMUTE 2       /* column permutation of A and jpvt */
 #define RQ_PHASE_PANEL 3         /* Householder panel + compact-WY T */
@@ -147,10 +148,45 @@ int rq_rqrcp_noalloc(int prec, int m, int n, void* A, int lda, int b, int p, int
                      int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
 
 /*
+ * rq_gaussian -- fills Omega (l x m, column-major, leading dimension ldo)
+ * with i.i.d. standard normal draws, the Gaussian compression matrix of
+ * Sec. 3.1 (and, with substream J, the fresh l x m_t matrix that repeated
+ * sampling draws for block J + 1, Sec. 3.4).  The draws are a pure function
+ * of (seed, substream, i + j l): Philox4x32-10 (Salmon et al., SC'11) keyed by
+ * the 64-bit seed, counter (t, substream) with t = (i + j l) / 2, two 52-bit
+ * uniforms per call, Box-Muller in FP64.  They do not depend on ldo, the
+ * stream or the GPU, and an l x m draw is the first m columns of an l x m'
+ * draw for m' > m.
+ *   prec   RQ_FP64 writes double; RQ_FP32 and RQ_MIXED write float (the FP64
+ *          value rounded to nearest).
+ *   Omega  device buffer of ldo * m elements, owned by the caller; entries
+ *          with row index >= l are left untouched.
+ * Errors: -(argument index) for l < 1, m < 1, Omega == NULL or ldo < l;
+ * RQ_ECUDA if the launch fails.  Asynchronous on stream.
+ */
+int rq_gaussian(rq_handle h, int prec, uint64_t seed, uint64_t substream, int l, int m, void* Omega, int ldo,
+                rq_stream stream);
+
+/*
+ * rq_rsrqrcp -- RQRCP with repeated sampling (RSRQRCP, Sec. 3.4): the
+ * ablation of the sample update.  Instead of refreshing the sample with
+ * Eq. (update1), every block after the first draws a fresh l x m_t Gaussian
+ * Omega^(J) and sketches the updated trailing matrix again, B = Omega^(J)
+ * A(j0+b:m, j0+b:n), at an extra 2 l m_t n_t flops and one more pass over the
+ * trailing matrix per block; the paper's update formula exists to avoid it.
+ * The draws come from rq_gaussian's generator: the first sample uses
+ * (seed, substream 0) at l x m, block J's fresh draws (seed, substream J) at
+ * l x (m - J b).  Outputs, precisions and errors as rq_rqrcp (argument
+ * indices follow this signature: seed is 10, tau 11, jpvt 12, info 13).
+ */
+int rq_rsrqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k, uint64_t seed,
+               void* tau, int* jpvt, int* info, rq_stream stream);
+
+/*
  * rq_qr -- unpivoted blocked Householder QR with the same panel and block
  * reflector kernels as rq_rqrcp but no sampling or pivoting: the QR the paper
- * compares RQRCP against ("identical to RQRCP after eliminating sample
- * operations and pivoting", Sec. 5.2, Table 3).  A is overwritten as in
+ * compares RQRCP against, which is RQRCP with the sampling and pivoting
+ * steps removed (Sec. 5.2, Table 3).  A is overwritten as in
  * rq_rqrcp with k = min(m, n); tau has min(m, n) entries.
  */
 int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* tau, int* info,

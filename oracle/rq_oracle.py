@@ -23,8 +23,8 @@ notes):
   recomputed from the remaining rows when the downdated value falls to
   ``sqrt(eps)`` times the value it had when last computed exactly.
 * The sample update (Eq. update1) is evaluated as
-  B_1 = S_12 - Omegahat_11 R_12 with Omegahat_11 = S_11 R_11^{-1} (Sec. 3.4:
-  "Omegahat_11 can then be recovered from S_11"); a zero diagonal of R_11
+  B_1 = S_12 - Omegahat_11 R_12 with Omegahat_11 = S_11 R_11^{-1} (Sec. 3.4
+  obtains Omegahat_11 from S_11 and R_11); a zero diagonal of R_11
   zeroes the corresponding column of Omegahat_11.
 """
 from __future__ import annotations
@@ -167,7 +167,7 @@ def qrcp(A, ncols=None):
 
 
 # ----------------------------------------------------------------------------
-# Partial QRCP of the sample (Sec. 3.2, Alg. 4 line "Get b column pivots")
+# Partial QRCP of the sample (Sec. 3.2; the pivot step of Alg. 4)
 # ----------------------------------------------------------------------------
 
 @dataclass

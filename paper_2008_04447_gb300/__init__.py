@@ -11,9 +11,9 @@ The compute path is the CUDA library ``librqrcp.so`` (C ABI in
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_OP_TRQRCP,  # noqa: F401
+from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_OP_RSRQRCP, RQ_OP_TRQRCP,  # noqa: F401
                    RQ_OP_TUXV, rq_create, rq_destroy, rq_last_error, rq_launch_count, rq_profile_enable,
-                   rq_profile_read, rq_qr, rq_rqrcp, rq_set_workspace, rq_trqrcp, rq_tuxv, rq_tuxv_batched,
+                   rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp, rq_tuxv, rq_tuxv_batched,
                    rq_workspace_size)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
@@ -87,6 +87,19 @@ class Handle:
         self._check(rc, "rq_rqrcp")
         return tau, jpvt, info
 
+    def rsrqrcp(self, A, seed, b, p, k=None, prec=None, stream=None):
+        """In-place RQRCP with repeated sampling (Sec. 3.4): fresh Gaussian draws of
+        (seed, J) sketch the trailing matrix at every block.  Returns (tau, jpvt, info)."""
+        import torch
+        m, n = A.shape
+        k = min(m, n) if k is None else k
+        prec = _prec_of(A) if prec is None else prec
+        tau = torch.empty(k, dtype=A.dtype, device=A.device)
+        jpvt = torch.empty(n, dtype=torch.int32, device=A.device)
+        info = torch.empty(1, dtype=torch.int32, device=A.device)
+        self._check(rq_rsrqrcp(self.h, prec, m, n, A, _ld(A), b, p, k, seed, tau, jpvt, info, stream), "rq_rsrqrcp")
+        return tau, jpvt, info
+
     def trqrcp(self, A, Omega, b, p, k, prec=None, stream=None):
         """Truncated RQRCP (Alg. 5); A is read only.  Returns (Y, tau, R, jpvt, info)."""
         import torch
@@ -148,6 +161,15 @@ class Handle:
         self._check(rc, "rq_tuxv_batched")
         self._keep = d  # the descriptors must outlive the asynchronous launch
         return outputs, info
+
+    def gaussian(self, l, m, seed, substream=0, dtype=None, out=None, stream=None):
+        """l x m column-major Gaussian draws of (seed, substream) (Sec. 3.1's Omega)."""
+        import torch
+        if out is None:
+            out = torch.empty((m, l), dtype=dtype or torch.float64, device="cuda").t()
+        prec = _prec_of(out)
+        self._check(rq_gaussian(self.h, prec, seed, substream, l, m, out, _ld(out), stream), "rq_gaussian")
+        return out
 
     def qr(self, A, b, prec=None, stream=None):
         """In-place unpivoted blocked Householder QR of column-major A."""

@@ -26,7 +26,7 @@ RQ_ETOOBIG = -1005
 RQ_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 RQ_FP64, RQ_FP32, RQ_MIXED = 0, 1, 2
-RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR = 0, 1, 2, 3
+RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR, RQ_OP_RSRQRCP = 0, 1, 2, 3, 4
 PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing", "sample_update", "other"]
 
 _P = ctypes.c_void_p
@@ -46,6 +46,8 @@ _SIGS = {
     "rq_trqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _P, _P], _I),
     "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
+    "rq_rsrqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, ctypes.c_uint64, _P, _P, _P, _P], _I),
+    "rq_gaussian": ([_P, _I, ctypes.c_uint64, ctypes.c_uint64, _I, _I, _P, _I, _P], _I),
 }
 
 # rq_problem: twelve int32 then seven 64-bit device pointers (104 bytes)
@@ -163,6 +165,16 @@ def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, s
 
 def rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, stream=None):
     return load().rq_tuxv_batched(h, prec, count, _ptr(problems), max_m, max_n, max_k, max_b, max_p, _stream(stream))
+
+
+def rq_rsrqrcp(h, prec, m, n, A, lda, b, p, k, seed, tau, jpvt, info, stream=None):
+    return load().rq_rsrqrcp(h, prec, m, n, _ptr(A), lda, b, p, k, seed & 0xFFFFFFFFFFFFFFFF, _ptr(tau), _ptr(jpvt),
+                             _ptr(info), _stream(stream))
+
+
+def rq_gaussian(h, prec, seed, substream, l, m, Omega, ldo, stream=None):
+    return load().rq_gaussian(h, prec, seed & 0xFFFFFFFFFFFFFFFF, substream & 0xFFFFFFFFFFFFFFFF, l, m, _ptr(Omega),
+                              ldo, _stream(stream))
 
 
 def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):

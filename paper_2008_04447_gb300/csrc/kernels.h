@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
+#include <cstdint>
 
 #include "rqrcp.h"
 
@@ -124,6 +125,11 @@ cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, ch
                          int* counter, bool mixed);
 
 cudaError_t iota(const Ctx& c, int* v, int n);
+
+// Omega (l x m, leading dimension ldo) = the Gaussian draws of (seed,
+// substream): Philox4x32-10 counters keyed by the seed, Box-Muller in FP64.
+template <typename T>
+cudaError_t gaussian(const Ctx& c, uint64_t seed, uint64_t substream, int l, int m, T* Omega, int ldo);
 // info = RQ_ETIMEOUT if the device error word is set, else the first j with
 // A(j-1, j-1) == 0 (1-based), else 0.
 template <typename TS>

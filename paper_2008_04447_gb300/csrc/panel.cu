@@ -1,4 +1,4 @@
-// Householder QR of one m_t x b panel (Alg. 4 "construct b reflectors"), with
+// Householder QR of one m_t x b panel (the b reflectors of Alg. 4), with
 // the compact-WY factor T of Sec. 4.1 built alongside.
 //
 // One cooperative launch per panel.  CTA c keeps rows [c*rpc, (c+1)*rpc) of

@@ -105,6 +105,7 @@ struct FactorWs {
   unsigned int* bar;
   int* err;
   TS *B0, *B1, *Ybuf, *YT, *Wt, *ptmp, *Tts;
+  TS* Om;  // l x m Gaussian draws (repeated sampling only)
   double *S11, *Oh, *T, *cand, *pscr;
   int *jtmp, *chg, *swaps, *src;
   char* splitk;
@@ -118,7 +119,7 @@ inline int pad4(int x) { return (x + 3) / 4 * 4; }
 inline size_t splitk_bytes_for(int b, int n, size_t elem) { return 16 * (size_t)b * n * elem; }
 
 template <typename TS>
-FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
+FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, bool resample = false) {
   Carver c(base);
   FactorWs<TS> w;
   w.bar = c.take<unsigned int>(4);
@@ -141,6 +142,7 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms) {
   w.pscr = c.take<double>(panel_scratch_doubles(b, num_sms));
   w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS));
   w.splitk = c.take<char>(w.splitk_bytes);
+  w.Om = resample ? c.take<TS>((size_t)l * m) : nullptr;
   w.bytes = align_up(c.off, 256);
   return w;
 }
@@ -190,15 +192,19 @@ cudaError_t prod_nn(const Ctx& c, int M, int N, int K, TS alpha, const TS* A, in
   return gemm<TS>(c, false, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
-// Blocked Householder QR, pivoted by the sample (Alg. 4) or unpivoted.
+// Blocked Householder QR, pivoted by the sample (Alg. 4) or unpivoted.  With
+// rs_seed (repeated sampling, Sec. 3.4) Omega is drawn from (seed, 0) and each
+// block's sample is a fresh sketch of the trailing matrix by the draws of
+// (seed, J) instead of the update of Eq. (update1).
 template <typename TS>
 int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega,
-               int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st) {
+               int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st, const uint64_t* rs_seed = nullptr) {
   const int l = pivot ? b + p : 1;
-  FactorWs<TS> w = carve_factor<TS>(nullptr, m, n, b, l, h->num_sms);
+  const bool rs = pivot && rs_seed != nullptr;
+  FactorWs<TS> w = carve_factor<TS>(nullptr, m, n, b, l, h->num_sms, rs);
   int rc = ensure_ws(h, w.bytes);
   if (rc) return rc;
-  w = carve_factor<TS>(h->ws, m, n, b, l, h->num_sms);
+  w = carve_factor<TS>(h->ws, m, n, b, l, h->num_sms, rs);
   Ctx c{st, h->num_sms, &h->launches, w.err, w.bar, w.splitk, w.splitk_bytes};
   cudaError_t e = cudaMemsetAsync(w.bar, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -206,6 +212,13 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
   TS* Bc = w.B0;
   TS* Bn = w.B1;
   const double sz = sizeof(TS);
+  if (rs) {
+    Phase ph(h, st, RQ_PHASE_OTHER, 0.0, sz * l * (double)m);
+    e = gaussian<TS>(c, *rs_seed, 0, l, m, w.Om, l);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gaussian");
+    Omega = w.Om;
+    ldo = l;
+  }
   if (pivot) {
     // Alg. 4: B = Omega A
     Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * l * (double)m * n, sz * ((double)m * n + (double)l * m + (double)l * n));
@@ -244,7 +257,7 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
         Tm = w.Tts;
       }
       {
-        // W^T = (Y T)^T A2 ; A2 -= Y W^T  (block reflector, Alg. 4 "finish b rows", "update")
+        // W^T = (Y T)^T A2 ; A2 -= Y W^T  (block reflector: the new R rows and the trailing update of Alg. 4)
         Phase ph(h, st, RQ_PHASE_TRAILING, 4.0 * mt * (double)n2 * bj + 2.0 * mt * (double)bj * bj,
                  sz * (3.0 * mt * (double)n2 + 2.0 * bj * (double)n2 + 3.0 * mt * (double)bj));
         e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, ldy, Tm, b, TS(0), w.YT, ldy);
@@ -252,7 +265,16 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
         if (e == cudaSuccess) e = prod_nn<TS>(c, mt, n2, bj, TS(-1), w.Ybuf, ldy, w.Wt, b, TS(1), A2, lda);
         if (e != cudaSuccess) return cuda_fail(h, e, "trailing update");
       }
-      if (pivot && j0 + bj < k) {
+      if (rs && j0 + bj < k) {
+        // Sec. 3.4, repeated sampling: B = Omega^(J) A(j0+bj:, j0+bj:), fresh draws of (seed, J)
+        const int m2 = mt - bj;
+        Phase ph(h, st, RQ_PHASE_SAMPLE_UPDATE, 2.0 * l * (double)m2 * n2,
+                 sz * ((double)m2 * n2 + 2.0 * l * (double)m2 + (double)l * n2));
+        e = gaussian<TS>(c, *rs_seed, (uint64_t)(j0 / b + 1), l, m2, w.Om, l);
+        if (e == cudaSuccess)
+          e = prod_nn<TS>(c, l, n2, m2, TS(1), w.Om, l, A2 + bj, lda, TS(0), Bn, l);
+        if (e != cudaSuccess) return cuda_fail(h, e, "resample");
+      } else if (pivot && j0 + bj < k) {
         // Eq. (update1): B1 = S12 - (S11 R11^{-1}) R12, B2 = S22
         Phase ph(h, st, RQ_PHASE_SAMPLE_UPDATE, (double)bj * bj * bj / 3.0 + (double)bj * bj * n2,
                  sz * 3.0 * bj * (double)n2);
@@ -372,7 +394,7 @@ int run_trqrcp(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, in
     {
       Phase ph(h, st, RQ_PHASE_PERMUTE, 0.0, 2.0 * sz * bj * (double)m);
       e = permute_index(c, bj, w.chg, w.src, jpvt + j0, w.jtmp);
-      // selected columns of A - Y^[J-1] W_1^T (Alg. 5 "construct selected columns")
+      // selected columns of A - Y^[J-1] W_1^T (Alg. 5)
       if (e == cudaSuccess) e = gather_columns<TS>(c, A, lda, m, jpvt + j0, bj, w.P, m);
       if (e != cudaSuccess) return cuda_fail(h, e, "gather");
     }
@@ -397,7 +419,7 @@ int run_trqrcp(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, in
     }
     const TS* Y2 = Y + j0 + (size_t)j0 * ldy;  // rows j0.. of the block's reflectors
     {
-      // W_2^T = T_2^T (Y_2^T A - (Y_2^T Y_1) W_1^T)  (Alg. 5, "form inner products")
+      // W_2^T = T_2^T (Y_2^T A - (Y_2^T Y_1) W_1^T)  (Alg. 5)
       Phase ph(h, st, RQ_PHASE_TRAILING,
                2.0 * bj * (double)mt * n + 2.0 * bj * (double)mt * j0 + 2.0 * bj * (double)j0 * n +
                    2.0 * bj * (double)bj * n,
@@ -646,9 +668,10 @@ int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b,
   if (p < 0) return -8;
   if (!bytes) return -9;
   const int l = (op == RQ_OP_QR) ? 1 : b + p;
-  if (op == RQ_OP_RQRCP || op == RQ_OP_QR) {
-    *bytes = prec == RQ_FP64 ? carve_factor<double>(nullptr, m, n, b, l, h->num_sms).bytes
-                             : carve_factor<float>(nullptr, m, n, b, l, h->num_sms).bytes;
+  if (op == RQ_OP_RQRCP || op == RQ_OP_QR || op == RQ_OP_RSRQRCP) {
+    const bool rs = op == RQ_OP_RSRQRCP;
+    *bytes = prec == RQ_FP64 ? carve_factor<double>(nullptr, m, n, b, l, h->num_sms, rs).bytes
+                             : carve_factor<float>(nullptr, m, n, b, l, h->num_sms, rs).bytes;
     return RQ_OK;
   }
   if (op == RQ_OP_TUXV) {
@@ -748,6 +771,30 @@ int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p
   return fail(h, RQ_ENOTIMPL, "rq_rqrcp: RQ_MIXED is not provided for the full factorisation");
 }
 
+int rq_rsrqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k, uint64_t seed, void* tau,
+               int* jpvt, int* info, rq_stream stream) {
+  int rc = check_common(h, prec);
+  if (rc) return rc;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (!A) return -5;
+  if (lda < m) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (k < 1 || k > (m < n ? m : n)) return -9;
+  if (!tau) return -11;
+  if (!jpvt) return -12;
+  if (!info) return -13;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == RQ_FP64)
+    return run_factor<double>(h, true, m, n, static_cast<double*>(A), lda, b, p, k, nullptr, 0,
+                              static_cast<double*>(tau), jpvt, info, st, &seed);
+  if (prec == RQ_FP32)
+    return run_factor<float>(h, true, m, n, static_cast<float*>(A), lda, b, p, k, nullptr, 0,
+                             static_cast<float*>(tau), jpvt, info, st, &seed);
+  return fail(h, RQ_ENOTIMPL, "rq_rsrqrcp: RQ_MIXED is not provided for the full factorisation");
+}
+
 int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* tau, int* info, rq_stream stream) {
   int rc = check_common(h, prec);
   if (rc) return rc;
@@ -829,6 +876,26 @@ int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, 
   return run_tuxv<float>(h, m, n, static_cast<const float*>(A), lda, b, p, k, static_cast<const float*>(Omega), ldo,
                          static_cast<float*>(U), ldu, static_cast<float*>(X), ldx, static_cast<float*>(V), ldv,
                          static_cast<float*>(sigma), info, st, prec == RQ_MIXED);
+}
+
+int rq_gaussian(rq_handle h, int prec, uint64_t seed, uint64_t substream, int l, int m, void* Omega, int ldo,
+                rq_stream stream) {
+  int rc = check_common(h, prec);
+  if (rc) return rc;
+  if (l < 1) return -5;
+  if (m < 1) return -6;
+  if (!Omega) return -7;
+  if (ldo < l) return -8;
+  Ctx c{static_cast<cudaStream_t>(stream), h->num_sms, &h->launches, nullptr, nullptr};
+  cudaError_t e;
+  {
+    const double bytes = (double)l * m * (prec == RQ_FP64 ? 8.0 : 4.0);
+    Phase ph(h, c.stream, RQ_PHASE_OTHER, 0.0, bytes);
+    e = prec == RQ_FP64 ? gaussian<double>(c, seed, substream, l, m, static_cast<double*>(Omega), ldo)
+                        : gaussian<float>(c, seed, substream, l, m, static_cast<float*>(Omega), ldo);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "rq_gaussian");
+  return RQ_OK;
 }
 
 int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,

@@ -1,4 +1,4 @@
-// Partial QRCP of the sample matrix B (Sec. 3.2; Alg. 4, "get b column pivots").
+// Partial QRCP of the sample matrix B (Sec. 3.2; the pivot step of Alg. 4).
 //
 // One cooperative launch per block of pivots.  Each CTA holds a slab of the
 // sample's columns in shared memory (in the storage precision, row-major inside
