@@ -220,6 +220,21 @@ int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, 
             void* sigma, int* info, rq_stream stream);
 
 /*
+ * rq_tuxv_iter -- rq_tuxv with j_max >= 1 refinement steps (Alg. 6; Sec. 4.2
+ * on iterating the flip between row and column bases).  Step 1 is rq_tuxv's;
+ * an even step j forms Z = U^T A and takes its LQ (the QR of A^T U, one pass
+ * over A), giving a new V and X = R^T, LOWER triangular; an odd step j > 1
+ * forms Z = A V and takes its QR, giving a new U and an upper triangular X.
+ * Each step after the first costs 2 m n k flops and one pass over A, and the
+ * rank-k error never increases.  Arguments as rq_tuxv with jmax inserted
+ * after k (argument 10; jmax < 1 returns -10); sigma, if set, is the SVD of the
+ * final X.
+ */
+int rq_tuxv_iter(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k, int jmax,
+                 const void* Omega, int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv, void* sigma,
+                 int* info, rq_stream stream);
+
+/*
  * One problem of a batched TUXV call.  All pointers are device pointers owned
  * by the caller; sizes and leading dimensions as for rq_tuxv.  Layout: twelve
  * int32 then seven 64-bit pointers (104 bytes).
@@ -231,10 +246,10 @@ typedef struct rq_problem {
   const void* A;              /* m x n, read only */
   const void* Omega;          /* (b + p) x m */
   void* U;                    /* m x k (out) */
-  void* X;                    /* k x k (out), upper triangular */
+  void* X;                    /* k x k (out), upper triangular; diag(sigma) when sigma != NULL */
   void* V;                    /* n x k (out) */
-  void* sigma;                /* must be NULL: the core SVD is not part of the batched path */
-  int* info;                  /* 1 int32 (out): 0, or RQ_ENOTIMPL when sigma was set */
+  void* sigma;                /* NULL, or k entries (out): the core SVD as in rq_tuxv (FP64 Jacobi) */
+  int* info;                  /* 1 int32 (out): 0 */
 } rq_problem;
 
 /*
@@ -248,6 +263,10 @@ typedef struct rq_problem {
  *   prec      RQ_FP32 (FP32 sketch) or RQ_MIXED (sketch inputs rounded to
  *             BF16, FP32 accumulation); contractions FP32, Householder scalars,
  *             sample norms, T and the Omegahat_11 solve FP64.
+ * A problem with sigma != NULL also gets the core SVD of X (Sec. 4.2) with
+ * rq_tuxv's conventions: an FP64 one-sided Jacobi SVD of X inside the
+ * problem's CTA, U <- U Uh, V <- V Vh, X <- diag(sigma), sigma descending,
+ * each column of V with its largest-magnitude entry positive.
  * The call issues one memset and one kernel; it does not synchronise, so it
  * can be captured in a CUDA graph once the handle's workspace is large enough
  * (make one call, or rq_set_workspace, before capturing).

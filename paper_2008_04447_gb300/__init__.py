@@ -13,7 +13,8 @@ from __future__ import annotations
 from . import _lib
 from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_OP_RSRQRCP, RQ_OP_TRQRCP,  # noqa: F401
                    RQ_OP_TUXV, rq_create, rq_destroy, rq_last_error, rq_launch_count, rq_profile_enable,
-                   rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp, rq_tuxv, rq_tuxv_batched,
+                   rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp,
+                   rq_tuxv, rq_tuxv_batched, rq_tuxv_iter,
                    rq_workspace_size)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
@@ -115,8 +116,9 @@ class Handle:
         self._check(rc, "rq_trqrcp")
         return Y, tau, R, jpvt, info
 
-    def tuxv(self, A, Omega, b, p, k, svd=False, prec=None, stream=None):
-        """TUXV (Alg. 6, j_max = 1): A ~= U X V^T.  Returns (U, X, V, sigma or None, info)."""
+    def tuxv(self, A, Omega, b, p, k, svd=False, prec=None, stream=None, jmax=1):
+        """TUXV (Alg. 6): A ~= U X V^T after jmax refinement steps (X upper
+        triangular for odd jmax, lower for even).  Returns (U, X, V, sigma or None, info)."""
         import torch
         m, n = A.shape
         prec = _prec_of(A) if prec is None else prec
@@ -125,14 +127,20 @@ class Handle:
         V = torch.empty((k, n), dtype=A.dtype, device=A.device).t()
         sigma = torch.empty(k, dtype=A.dtype, device=A.device) if svd else None
         info = torch.empty(1, dtype=torch.int32, device=A.device)
-        rc = rq_tuxv(self.h, prec, m, n, A, _ld(A), b, p, k, Omega, _ld(Omega), U, m, X, k, V, n, sigma, info, stream)
+        if jmax == 1:
+            rc = rq_tuxv(self.h, prec, m, n, A, _ld(A), b, p, k, Omega, _ld(Omega), U, m, X, k, V, n, sigma, info,
+                         stream)
+        else:
+            rc = rq_tuxv_iter(self.h, prec, m, n, A, _ld(A), b, p, k, jmax, Omega, _ld(Omega), U, m, X, k, V, n, sigma,
+                              info, stream)
         self._check(rc, "rq_tuxv")
         return U, X, V, sigma, info
 
-    def tuxv_batched(self, problems, prec=RQ_MIXED, stream=None, outputs=None):
+    def tuxv_batched(self, problems, prec=RQ_MIXED, stream=None, outputs=None, svd=False):
         """Batched TUXV of [(A, Omega, b, p, k), ...] (column-major FP32 device tensors).
 
-        One persistent launch; returns [(U, X, V), ...] and the info tensor.
+        One persistent launch; returns [(U, X, V), ...] (with svd, the core SVD of
+        every problem: [(U, X = diag(sigma), V, sigma), ...]) and the info tensor.
         The descriptors are built on the host and copied to the device.
         """
         import numpy as np
@@ -144,13 +152,16 @@ class Handle:
                 m, n = A.shape
                 outputs.append((torch.empty((k, m), dtype=A.dtype, device=dev).t(),
                                 torch.empty((k, k), dtype=A.dtype, device=dev).t(),
-                                torch.empty((k, n), dtype=A.dtype, device=dev).t()))
+                                torch.empty((k, n), dtype=A.dtype, device=dev).t())
+                               + ((torch.empty(k, dtype=A.dtype, device=dev),) if svd else ()))
         info = torch.zeros(len(problems), dtype=torch.int32, device=dev)
         desc = np.zeros(len(problems), dtype=_lib.problem_dtype())
-        for i, ((A, Om, b, p, k), (U, X, V)) in enumerate(zip(problems, outputs)):
+        for i, ((A, Om, b, p, k), out) in enumerate(zip(problems, outputs)):
             m, n = A.shape
+            U, X, V = out[:3]
+            sg = out[3].data_ptr() if len(out) > 3 and out[3] is not None else 0
             desc[i] = (m, n, k, b, p, _ld(A), _ld(Om), _ld(U), _ld(X), _ld(V), 0, 0, A.data_ptr(), Om.data_ptr(),
-                       U.data_ptr(), X.data_ptr(), V.data_ptr(), 0, info.data_ptr() + 4 * i)
+                       U.data_ptr(), X.data_ptr(), V.data_ptr(), sg, info.data_ptr() + 4 * i)
         d = torch.from_numpy(desc.view(np.uint8)).to(dev)
         mm = max(int(A.shape[0]) for A, *_ in problems)
         mn = max(int(A.shape[1]) for A, *_ in problems)

@@ -45,6 +45,7 @@ _SIGS = {
     "rq_qr": ([_P, _I, _I, _I, _P, _I, _I, _P, _P, _P], _I),
     "rq_trqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _P, _P, _P], _I),
     "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
+    "rq_tuxv_iter": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
     "rq_rsrqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, ctypes.c_uint64, _P, _P, _P, _P], _I),
     "rq_gaussian": ([_P, _I, ctypes.c_uint64, ctypes.c_uint64, _I, _I, _P, _I, _P], _I),
@@ -184,6 +185,11 @@ def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):
 def rq_trqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, Y, ldy, tau, R, ldr, jpvt, info, stream=None):
     return load().rq_trqrcp(h, prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(Y), ldy, _ptr(tau),
                             _ptr(R), ldr, _ptr(jpvt), _ptr(info), _stream(stream))
+
+
+def rq_tuxv_iter(h, prec, m, n, A, lda, b, p, k, jmax, Omega, ldo, U, ldu, X, ldx, V, ldv, sigma, info, stream=None):
+    return load().rq_tuxv_iter(h, prec, m, n, _ptr(A), lda, b, p, k, jmax, _ptr(Omega), ldo, _ptr(U), ldu, _ptr(X),
+                               ldx, _ptr(V), ldv, _ptr(sigma), _ptr(info), _stream(stream))
 
 
 def rq_tuxv(h, prec, m, n, A, lda, b, p, k, Omega, ldo, U, ldu, X, ldx, V, ldv, sigma, info, stream=None):

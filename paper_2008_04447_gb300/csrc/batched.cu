@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -27,17 +29,7 @@ constexpr int kMaxLB = 128;  // largest sample rank of the batched path
 // the live sample or the current panel when they fit, so that the serial
 // pivot / reflector steps run out of shared memory instead of L2.
 constexpr int kStageFloats = 50 * 1024;  // 200 KB
-
-__device__ __forceinline__ float bsum_f(float v, float* red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) t += red[w];
-  return t;
-}
+constexpr int kMaxDevices = 64;
 
 __device__ __forceinline__ double bsum_d(double v, double* red) {
   v = warp_sum(v);
@@ -361,8 +353,8 @@ __device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, doubl
 }
 
 struct Slot {
-  float *B, *Wt, *Z, *Y, *P, *Xt, *G, *Wsel, *taus, *Tf, *Zt, *Z1, *Yq, *YTq, *Wq, *tauq;
-  double *nu2, *ref2, *S11, *Oh, *T, *Tq;
+  float *B, *Wt, *Z, *Y, *P, *Xt, *G, *Wsel, *taus, *Tf, *Zt, *Z1, *Yq, *YTq, *Wq, *tauq, *Uh, *Vh;
+  double *nu2, *ref2, *S11, *Oh, *T, *Tq, *jac;
   int* jp;
   size_t bytes;
 };
@@ -401,6 +393,11 @@ __host__ __device__ inline Slot carve_slot(char* base, int m, int n, int k, int 
   s.T = (double*)take(sizeof(double) * (size_t)b * b);
   s.Tq = (double*)take(sizeof(double) * (size_t)nb * b * b);
   s.jp = (int*)take(sizeof(int) * (size_t)n);
+  // core SVD (problems that ask for sigma): FP64 W, V and norms when they do
+  // not fit in shared memory; the FP32 rotations Uh, Vh
+  s.jac = (double*)take(sizeof(double) * (2 * (size_t)k * k + k));
+  s.Uh = (float*)take(sizeof(float) * (size_t)k * k);
+  s.Vh = (float*)take(sizeof(float) * (size_t)k * k);
   s.bytes = (off + 255) / 256 * 256;
   return s;
 }
@@ -589,6 +586,140 @@ __device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool
   __syncthreads();
 }
 
+constexpr int kMaxSweepsB = 40;
+
+// Core SVD of the k x k upper triangular X (Sec. 4.2; FP64 one-sided Jacobi,
+// Hestenes' method): X Vh = Uh diag(sigma), then U <- U Uh, V <- V Vh and
+// X <- diag(sigma), sigma descending (ties to the lower column), and each
+// column of V with its largest-magnitude entry (lowest row on ties) positive,
+// U's column following.  A round rotates kk/2 disjoint column pairs (circle
+// method), one warp per pair; a sweep is kk - 1 rounds; sweeps stop when one
+// rotates nothing.  W and V live in the staging area when they fit.
+__device__ void core_svd_b(const rq_problem& pr, Slot& w, float* sm) {
+  const int m = pr.m, n = pr.n, k = pr.k;
+  float* U = static_cast<float*>(pr.U);
+  float* X = static_cast<float*>(pr.X);
+  float* V = static_cast<float*>(pr.V);
+  float* sig = static_cast<float*>(pr.sigma);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t k2 = (size_t)k * k;
+  const size_t cap = (size_t)kStageFloats * sizeof(float) / sizeof(double);
+  double* dsm = reinterpret_cast<double*>(sm);
+  double* W = k2 <= cap ? dsm : w.jac;
+  double* Vr = 2 * k2 <= cap ? dsm + k2 : w.jac + k2;
+  double* nrm = w.jac + 2 * k2;
+  for (size_t e = tid; e < k2; e += NT) {
+    const int i = e % k, j = e / k;
+    W[e] = (double)X[i + (size_t)j * pr.ldx];
+    Vr[e] = i == j ? 1.0 : 0.0;
+  }
+  __shared__ int s_rot;
+  const int kk = (k + 1) / 2 * 2, npairs = kk / 2;
+  const double tol = (k > 1 ? (double)k : 2.0) * 2.220446049250313e-16;
+  __syncthreads();
+  for (int sweep = 0; sweep < kMaxSweepsB; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < kk - 1; ++r) {
+      for (int pi = warp; pi < npairs; pi += NW) {
+        // circle method: position 0 fixed, positions 1..kk-1 rotate by r
+        int p = pi == 0 ? 0 : 1 + (pi - 1 + r) % (kk - 1);
+        const int pos = kk - 1 - pi;
+        int q = 1 + (pos - 1 + r) % (kk - 1);
+        if (p >= k || q >= k) continue;
+        if (p > q) { const int t = p; p = q; q = t; }
+        double* wp = W + (size_t)p * k;
+        double* wq = W + (size_t)q * k;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wp[i], y = wq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        // butterfly sums: every lane holds the same bits, so all take the same branch
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+          double* vp = Vr + (size_t)p * k;
+          double* vq = Vr + (size_t)q * k;
+          for (int i = lane; i < k; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = c * x - sn * y;
+            wq[i] = sn * x + c * y;
+            const double u = vp[i], v = vq[i];
+            vp[i] = c * u - sn * v;
+            vq[i] = sn * u + c * v;
+          }
+          if (lane == 0) atomicAdd(&s_rot, 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = s_rot;
+    __syncthreads();
+    if (rotated == 0) break;
+  }
+  for (int j = warp; j < k; j += NW) {
+    double a2 = 0.0;
+    for (int i = lane; i < k; i += 32) a2 = fma(W[i + (size_t)j * k], W[i + (size_t)j * k], a2);
+    a2 = warp_sum(a2);
+    if (lane == 0) nrm[j] = sqrt(a2);
+  }
+  __syncthreads();
+  for (int j = warp; j < k; j += NW) {
+    const double sj = nrm[j];
+    int cnt = 0;
+    for (int i = lane; i < k; i += 32) {
+      const double si = nrm[i];
+      cnt += (si > sj || (si == sj && i < j)) ? 1 : 0;
+    }
+    const int rk = warp_sum(cnt);
+    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    for (int i = lane; i < k; i += 32) {
+      w.Uh[i + (size_t)rk * k] = (float)(W[i + (size_t)j * k] * inv);
+      w.Vh[i + (size_t)rk * k] = (float)Vr[i + (size_t)j * k];
+    }
+    if (lane == 0) sig[rk] = (float)sj;
+  }
+  __syncthreads();
+  // U <- U Uh and V <- V Vh through the (now free) Z1 (m x k) and Zt (n x k)
+  gemm_b<false, false>(m, k, k, 1.f, U, pr.ldu, w.Uh, k, 0.f, w.Z1, m, sm);
+  gemm_b<false, false>(n, k, k, 1.f, V, pr.ldv, w.Vh, k, 0.f, w.Zt, n, sm);
+  __syncthreads();
+  for (size_t e = tid; e < (size_t)m * k; e += NT) U[(e % m) + (e / m) * pr.ldu] = w.Z1[e];
+  for (size_t e = tid; e < (size_t)n * k; e += NT) V[(e % n) + (e / n) * pr.ldv] = w.Zt[e];
+  __syncthreads();
+  for (int j = warp; j < k; j += NW) {
+    float* v = V + (size_t)j * pr.ldv;
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      const float x = fabsf(v[i]);
+      if (x > best || (x == best && i < bi)) { best = x; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (b2 > best || (b2 == best && i2 < bi)) { best = b2; bi = i2; }
+    }
+    if (bi < n && v[bi] < 0.f) {
+      for (int i = lane; i < n; i += 32) v[i] = -v[i];
+      float* u = U + (size_t)j * pr.ldu;
+      for (int i = lane; i < m; i += 32) u[i] = -u[i];
+    }
+  }
+  for (size_t e = tid; e < k2; e += NT) {
+    const int i = e % k, j = e / k;
+    X[i + (size_t)j * pr.ldx] = i == j ? sig[i] : 0.f;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) tuxv_batched_kernel(BatchArgs a) {
   extern __shared__ float sm[];
   __shared__ Shm s;
@@ -601,12 +732,9 @@ __global__ void __launch_bounds__(NT) tuxv_batched_kernel(BatchArgs a) {
     __syncthreads();
     if (idx >= a.count) break;
     const rq_problem pr = a.problems[idx];
-    if (pr.sigma != nullptr) {  // the core SVD is not part of the batched path
-      if (threadIdx.x == 0 && pr.info) *pr.info = RQ_ENOTIMPL;
-      continue;
-    }
     Slot w = carve_slot(base, pr.m, pr.n, pr.k, pr.b, pr.b + pr.p);
     solve_one(pr, w, s, sm, a.mixed != 0);
+    if (pr.sigma != nullptr) core_svd_b(pr, w, sm);
   }
 }
 
@@ -621,15 +749,37 @@ int batched_limits_ok(int max_b, int max_p) { return max_b >= 1 && max_b <= kMax
 constexpr size_t kBatchSmem = (size_t)kStageFloats * sizeof(float);
 static_assert(kStageFloats >= 2 * 32 * (128 + 32 + 2), "the GEMM tiles share the staging area");
 
+// Per device, once: raise the kernel's dynamic shared memory limit and record
+// how many CTAs fit on an SM.  Later calls make no CUDA runtime call here, so a
+// call captured into a CUDA graph issues only the memset and the launch.
+int batched_ctas_per_sm() {
+  static std::mutex mu;
+  static int per_sm_of[kMaxDevices] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (per_sm_of[dev] == 0) {
+    const size_t smem = kBatchSmem;
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(tuxv_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tuxv_batched_kernel, NT, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      return -1;
+    }
+    per_sm_of[dev] = per_sm;
+  }
+  return per_sm_of[dev];
+}
+
 cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
                          int* counter, bool mixed) {
   const size_t smem = kBatchSmem;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t ea = cudaFuncSetAttribute(tuxv_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ea != cudaSuccess) return ea;
-    attr = true;
-  }
+  if (batched_ctas_per_sm() < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
   if (e != cudaSuccess) return e;
   BatchArgs a{problems, count, ws, slot_bytes, counter, mixed ? 1 : 0};
@@ -639,13 +789,8 @@ cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, ch
 }
 
 int batched_slots(int num_sms) {
-  int per_sm = 0;
-  const size_t smem = kBatchSmem;
-  cudaFuncSetAttribute(tuxv_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tuxv_batched_kernel, NT, smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return per_sm * num_sms;
+  const int per_sm = batched_ctas_per_sm();
+  return (per_sm < 1 ? 1 : per_sm) * num_sms;
 }
 
 }  // namespace rq

@@ -560,11 +560,14 @@ TuxvWs<TS> carve_tuxv(void* base, int m, int n, int k, int b, int l, int num_sms
   return w;
 }
 
-// TUXV, Alg. 6 with j_max = 1: TRQRCP -> Z0 = R P^T -> LQ of Z0 (QR of Z0^T,
-// V explicit) -> Z1 = A V -> QR of Z1 (U explicit, X = R) -> optional core SVD.
+// TUXV, Alg. 6: TRQRCP -> Z0 = R P^T -> LQ of Z0 (QR of Z0^T, V explicit) ->
+// Z1 = A V -> QR of Z1 (U explicit, X = R); for j = 2..jmax the refinement
+// alternates (even j: Z = U^T A, LQ through the QR of A^T U, V explicit and
+// X = R^T lower triangular; odd j: Z = A V, QR as for j = 1) -> optional core SVD.
 template <typename TS>
 int run_tuxv(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, int k, const TS* Omega, int ldo, TS* U,
-             int ldu, TS* X, int ldx, TS* V, int ldv, TS* sigma, int* info, cudaStream_t st, bool mixed = false) {
+             int ldu, TS* X, int ldx, TS* V, int ldv, TS* sigma, int* info, cudaStream_t st, bool mixed = false,
+             int jmax = 1) {
   const int l = b + p;
   TuxvWs<TS> w = carve_tuxv<TS>(nullptr, m, n, k, b, l, h->num_sms);
   int rc = ensure_ws(h, w.bytes);
@@ -596,6 +599,24 @@ int run_tuxv(rq_handle h, int m, int n, const TS* A, int lda, int b, int p, int 
     Phase ph(h, st, RQ_PHASE_OTHER, 4.0 * m * (double)k * k, sz * 6.0 * m * (double)k);
     e = qr_explicit<TS>(c, w.Z1, m, m, k, b, w.qs, U, ldu, X, ldx);
     if (e != cudaSuccess) return cuda_fail(h, e, "QR of Z1");
+  }
+  for (int j = 2; j <= jmax; ++j) {
+    if (j % 2 == 0) {
+      // Z^(j) = U^T A: its LQ through the QR of Z^T = A^T U (n x k); X = R^T
+      Phase ph(h, st, RQ_PHASE_TRAILING, 2.0 * m * (double)n * k + 4.0 * n * (double)k * k,
+               sz * ((double)m * n + (double)m * k + 6.0 * (double)n * k));
+      e = prod_tn_skinny<TS>(c, n, k, m, A, lda, U, ldu, w.Zt, n);
+      if (e == cudaSuccess) e = qr_explicit<TS>(c, w.Zt, n, n, k, b, w.qs, V, ldv, w.Vh, k);
+      if (e == cudaSuccess) e = transpose<TS>(c, k, k, w.Vh, k, X, ldx);
+      if (e != cudaSuccess) return cuda_fail(h, e, "LQ of U^T A");
+    } else {
+      // Z^(j) = A V and its QR, as for j = 1
+      Phase ph(h, st, RQ_PHASE_TRAILING, 2.0 * m * (double)n * k + 4.0 * m * (double)k * k,
+               sz * ((double)m * n + (double)n * k + 6.0 * (double)m * k));
+      e = prod_nn<TS>(c, m, k, n, TS(1), A, lda, V, ldv, TS(0), w.Z1, m);
+      if (e == cudaSuccess) e = qr_explicit<TS>(c, w.Z1, m, m, k, b, w.qs, U, ldu, X, ldx);
+      if (e != cudaSuccess) return cuda_fail(h, e, "QR of A V");
+    }
   }
   if (sigma) {
     // core SVD of X: U <- U Uh, V <- V Vh, X <- diag(sigma)
@@ -876,6 +897,38 @@ int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, 
   return run_tuxv<float>(h, m, n, static_cast<const float*>(A), lda, b, p, k, static_cast<const float*>(Omega), ldo,
                          static_cast<float*>(U), ldu, static_cast<float*>(X), ldx, static_cast<float*>(V), ldv,
                          static_cast<float*>(sigma), info, st, prec == RQ_MIXED);
+}
+
+int rq_tuxv_iter(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k, int jmax,
+                 const void* Omega, int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv, void* sigma,
+                 int* info, rq_stream stream) {
+  int rc = check_common(h, prec);
+  if (rc) return rc;
+  if (m < 1) return -3;
+  if (n < 1) return -4;
+  if (!A) return -5;
+  if (lda < m) return -6;
+  if (b < 1) return -7;
+  if (p < 0) return -8;
+  if (k < 1 || k > (m < n ? m : n)) return -9;
+  if (jmax < 1) return -10;
+  if (!Omega) return -11;
+  if (ldo < b + p) return -12;
+  if (!U) return -13;
+  if (ldu < m) return -14;
+  if (!X) return -15;
+  if (ldx < k) return -16;
+  if (!V) return -17;
+  if (ldv < n) return -18;
+  if (!info) return -20;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == RQ_FP64)
+    return run_tuxv<double>(h, m, n, static_cast<const double*>(A), lda, b, p, k, static_cast<const double*>(Omega),
+                            ldo, static_cast<double*>(U), ldu, static_cast<double*>(X), ldx, static_cast<double*>(V),
+                            ldv, static_cast<double*>(sigma), info, st, false, jmax);
+  return run_tuxv<float>(h, m, n, static_cast<const float*>(A), lda, b, p, k, static_cast<const float*>(Omega), ldo,
+                         static_cast<float*>(U), ldu, static_cast<float*>(X), ldx, static_cast<float*>(V), ldv,
+                         static_cast<float*>(sigma), info, st, prec == RQ_MIXED, jmax);
 }
 
 int rq_gaussian(rq_handle h, int prec, uint64_t seed, uint64_t substream, int l, int m, void* Omega, int ldo,

@@ -110,3 +110,73 @@ def test_batched_fp32_matches_single_problem_path_quality(H):
         e0 = np.linalg.norm(a - (U.double() @ X.double() @ V.double().T).cpu().numpy())
         e1 = np.linalg.norm(a - (U1.double() @ X1.double() @ V1.double().T).cpu().numpy())
         assert abs(e0 - e1) <= 0.02 * e1
+
+
+def test_batched_core_svd(H):
+    """sigma != NULL: the batched kernel's FP64 Jacobi SVD of each core X.
+
+    The same problems without sigma give X bit for bit (one CTA per problem,
+    the same kernel path up to the core), so sigma must equal the singular
+    values of that X (numpy, FP64) to the FP32 rounding of the outputs, and
+    U diag(sigma) V^T must equal U X V^T.  k = 120 keeps V outside shared
+    memory and k = 170 both W and V.
+    """
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED
+    shapes = [(300, 200, 170, 64), (260, 180, 120, 32), (200, 150, 64, 32), (120, 90, 33, 16), (50, 40, 7, 7),
+              (30, 20, 1, 1)]
+    host = [(I.graded(m, n, 6, seed=40 + i), I.omega(b + 8, m, seed=60 + i), b, 8, k)
+            for i, (m, n, k, b) in enumerate(shapes)]
+    dev = _to_dev(host)
+    plain, info0 = H.tuxv_batched(dev, prec=RQ_MIXED)
+    outs, info = H.tuxv_batched(dev, prec=RQ_MIXED, svd=True)
+    torch.cuda.synchronize()
+    assert int(info.abs().sum()) == 0 and int(info0.abs().sum()) == 0
+    for (a, om, b, p, k), (U0, X0, V0), (U, X, V, s) in zip(host, plain, outs):
+        U0, X0, V0 = (t.cpu().double().numpy() for t in (U0, X0, V0))
+        U, X, V, s = (t.cpu().double().numpy() for t in (U, X, V, s))
+        sv = np.linalg.svd(X0, compute_uv=False)
+        assert np.all(np.abs(s - sv) <= 1e-6 * sv[0] + 2e-7 * sv), (k, np.max(np.abs(s - sv)) / sv[0])
+        assert np.all(np.diff(s) <= 0)
+        assert np.array_equal(X, np.diag(s))
+        assert np.allclose(U.T @ U, np.eye(k), atol=1e-5)
+        assert np.allclose(V.T @ V, np.eye(k), atol=1e-5)
+        idx = np.argmax(np.abs(V), axis=0)
+        assert np.all(V[idx, np.arange(k)] > 0)
+        nrm = np.linalg.norm(a)
+        assert np.linalg.norm((U * s) @ V.T - U0 @ X0 @ V0.T) <= 1e-5 * nrm
+
+
+def test_batched_graph_capture_and_replay(H):
+    """The batched call captured in a CUDA graph replays to the same bits, and
+    reads its inputs at replay time (A scaled by 2 gives X scaled by 2 exactly:
+    every step is homogeneous and powers of two round exactly)."""
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED, rq_tuxv_batched
+    host = _mix(16, seed=7)
+    dev = _to_dev(host)
+    outs, info = H.tuxv_batched(dev, prec=RQ_MIXED)       # sizes the workspace, uploads descriptors
+    torch.cuda.synchronize()
+    ref = [tuple(t.clone() for t in o) for o in outs]
+    desc = H._keep
+    dims = (max(int(t[0].shape[0]) for t in dev), max(int(t[0].shape[1]) for t in dev), max(t[4] for t in dev),
+            max(t[2] for t in dev), max(t[3] for t in dev))
+    for o in outs:
+        for t in o:
+            t.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = rq_tuxv_batched(H.h, RQ_MIXED, len(dev), desc, *dims)
+    assert rc == 0
+    assert all(torch.count_nonzero(t) == 0 for o in outs for t in o)   # captured, not run
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        for t, u in zip(o, r):
+            assert torch.equal(t, u)
+    dev[0][0].mul_(2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    U, X, V = outs[0]
+    assert torch.equal(U, ref[0][0]) and torch.equal(V, ref[0][2])
+    assert torch.equal(X, 2.0 * ref[0][1])

@@ -97,3 +97,65 @@ def test_tuxv_error_bounds(H):
     s = np.linalg.svd(a, compute_uv=False)
     assert err <= err_tr * (1 + 1e-10)
     assert err >= np.sqrt(np.sum(s[k:] ** 2)) * (1 - 1e-10)
+
+
+@pytest.mark.parametrize("jmax", [2, 3, 4])
+def test_tuxv_iterations_match_oracle(H, jmax):
+    """rq_tuxv_iter (Alg. 6 with j_max > 1) against the oracle's iterations:
+    U X V^T within 1e-12 ||A||_F, X lower triangular after an even step and
+    upper after an odd one, X entry by entry within 1e-12 ||A||_F when no
+    sample decision is a near-tie, and the rank-k error non-increasing in j."""
+    import torch
+    m, n, k, b, p = 600, 400, 48, 16, 8
+    a = I.graded(m, n, 3, seed=17)     # slow decay: the refinement changes the error
+    om = I.omega(b + p, m, seed=18)
+    A, Om = to_dev(a), to_dev(om)
+    U, X, V, _, info = H.tuxv(A, Om, b, p, k, jmax=jmax)
+    torch.cuda.synchronize()
+    U, X, V = to_host(U), to_host(X), to_host(V)
+    ref = O.tuxv(a, om, b, k, jmax=jmax)
+    nrm = np.linalg.norm(a)
+    assert int(info.cpu()[0]) == 0
+    assert np.allclose(U.T @ U, np.eye(k), atol=1e-12)
+    assert np.allclose(V.T @ V, np.eye(k), atol=1e-12)
+    tri = np.tril(X) if jmax % 2 == 0 else np.triu(X)
+    assert np.array_equal(X, tri)
+    assert np.max(np.abs(U @ X @ V.T - ref.U @ ref.X @ ref.V.T)) <= 1e-12 * nrm
+    if first_near_tie(ref.tr.gaps, b, 1e-6) is None:
+        assert np.max(np.abs(X - ref.X)) <= 1e-12 * nrm
+    errs = []
+    for j in range(1, jmax + 1):
+        Uj, Xj, Vj, _, _ = H.tuxv(A, Om, b, p, k, jmax=j)
+        torch.cuda.synchronize()
+        errs.append(np.linalg.norm(a - to_host(Uj) @ to_host(Xj) @ to_host(Vj).T))
+    assert all(e2 <= e1 * (1 + 1e-12) for e1, e2 in zip(errs, errs[1:]))
+    assert errs[-1] < errs[0]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_tuxv_iterations_with_core_svd(H, mode):
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED
+    m, n, k, b, p = 500, 700, 40, 16, 8
+    a = I.graded(m, n, 3, seed=27)
+    om = I.omega(b + p, m, seed=28)
+    if mode == "mixed":
+        a32, o32 = (np.asarray(x, np.float32).astype(np.float64) for x in (a, om))
+        U, X, V, s, info = H.tuxv(to_dev(a32, torch.float32), to_dev(o32, torch.float32), b, p, k, svd=True,
+                                  prec=RQ_MIXED, jmax=2)
+        ref = O.tuxv(a32, o32, b, k, jmax=2, svd=True, sketch_inputs="bf16")
+        tol_s, tol_o = 1e-5, 1e-5
+    else:
+        U, X, V, s, info = H.tuxv(to_dev(a), to_dev(om), b, p, k, svd=True, jmax=2)
+        ref = O.tuxv(a, om, b, k, jmax=2, svd=True)
+        tol_s, tol_o = 1e-12, 1e-12
+    torch.cuda.synchronize()
+    U, X, V, s = to_host(U), to_host(X), to_host(V), to_host(s)
+    assert np.all(np.diff(s) <= 0)
+    assert np.allclose(X, np.diag(s))
+    assert np.allclose(U.T @ U, np.eye(k), atol=tol_o) and np.allclose(V.T @ V, np.eye(k), atol=tol_o)
+    if first_near_tie(ref.tr.gaps, b, 1e-6 if mode == "fp64" else 1e-4) is None:
+        assert np.max(np.abs(s - ref.sigma)) <= tol_s * ref.sigma[0]
+    e = np.linalg.norm(a - (U * s) @ V.T)
+    e_ref = np.linalg.norm(a - ref.U @ ref.X @ ref.V.T)
+    assert e <= e_ref * (1 + (1e-10 if mode == "fp64" else 0.05))

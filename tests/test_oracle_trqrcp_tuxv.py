@@ -123,3 +123,32 @@ def test_tuxv_with_core_svd_and_more_iterations():
     e1 = np.linalg.norm(a - t1.U @ t1.X @ t1.V.T)
     e2 = np.linalg.norm(a - t2.U @ t2.X @ t2.V.T)
     assert e2 <= e1 * (1 + 1e-8)
+
+
+def test_tuxv_iterations_are_subspace_iteration():
+    """Alg. 6 with j_max > 1: each step is a projection, A ~= U U^T A or A V V^T,
+    so ||A - U X V^T||^2 = ||A||^2 - ||X||^2 at every step; X alternates between
+    lower (even j) and upper (odd j) triangular; the error never increases; and
+    the alternation is a subspace iteration, so the excess over the
+    Eckart-Young error, err^2 - sum_{i>k} sigma_i^2, shrinks by at least
+    (sigma_{k+1} / sigma_k)^2 = 1/4 per step once the transient has passed."""
+    m, n, k, b = 300, 200, 20, 8
+    rng = np.random.default_rng(5)
+    Uq, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.r_[np.linspace(2.0, 1.0, k), 0.5 * np.linspace(1.0, 0.1, n - k)]
+    a = (Uq * s) @ Vq.T
+    om = I.omega(b + 8, m, seed=6)
+    na2 = np.linalg.norm(a) ** 2
+    opt2 = np.sum(s[k:] ** 2)
+    excess = []
+    for j in range(1, 15):
+        t = O.tuxv(a, om, b, k, jmax=j)
+        err2 = np.linalg.norm(a - t.U @ t.X @ t.V.T) ** 2
+        assert abs(err2 - (na2 - np.linalg.norm(t.X) ** 2)) <= 1e-10 * na2
+        assert np.array_equal(t.X, np.tril(t.X) if j % 2 == 0 else np.triu(t.X))
+        assert np.allclose(t.U.T @ t.U, np.eye(k), atol=1e-12) and np.allclose(t.V.T @ t.V, np.eye(k), atol=1e-12)
+        excess.append(err2 - opt2)
+    assert all(e2 <= e1 for e1, e2 in zip(excess, excess[1:]))
+    assert all(e2 <= 0.25 * e1 for e1, e2 in zip(excess[2:], excess[3:]))
+    assert excess[0] > 0.1 * opt2 and excess[-1] <= 1e-9 * opt2
