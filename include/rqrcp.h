@@ -183,6 +183,25 @@ int rq_rsrqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int
                void* tau, int* jpvt, int* info, rq_stream stream);
 
 /*
+ * rq_latent_cdf -- host function (no GPU work).  The Bayesian analysis of the
+ * sample (Sec. 3.3): with a Gaussian sample of rank l and Jeffreys' prior, a
+ * column's latent squared norm is phi ||B_j||^2 / (l - 2), and this returns
+ * P(phi < tau | l) = Q(l/2, (l - 2) / (2 tau)) (the regularized upper
+ * incomplete gamma function; e.g. 0.30 % for l = 4, tau = 1/8) in *prob.
+ * Errors: -1 for l < 3, -2 for tau <= 0, -3 for prob == NULL.
+ *
+ * rq_padding -- host function.  The smallest padding p >= 2 such that every
+ * pivot decision of a block keeps P(phi < tau) <= delta: the i-th decision
+ * of a block sees a sample of effective rank l - i + 1, so the weakest is the
+ * last, at rank p + 1 (the paper's p = 8, b = 32 gives ranks 9 to 40).
+ * Errors: -1 unless 0 < tau < 1, -2 unless 0 < delta < 1, -3 for p == NULL,
+ * RQ_ENOTIMPL if no p <= RQ_PADDING_MAX is enough.
+ */
+#define RQ_PADDING_MAX 4096
+int rq_latent_cdf(int l, double tau, double* prob);
+int rq_padding(double tau, double delta, int* p);
+
+/*
  * rq_qr -- unpivoted blocked Householder QR with the same panel and block
  * reflector kernels as rq_rqrcp but no sampling or pivoting: the QR the paper
  * compares RQRCP against, which is RQRCP with the sampling and pivoting

@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_OP_RSRQRCP, RQ_OP_TRQRCP,  # noqa: F401
                    RQ_OP_TUXV, rq_create, rq_destroy, rq_last_error, rq_launch_count, rq_profile_enable,
                    rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp,
-                   rq_tuxv, rq_tuxv_batched, rq_tuxv_iter,
+                   rq_tuxv, rq_tuxv_batched, rq_tuxv_iter, rq_latent_cdf, rq_padding,
                    rq_workspace_size)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]

@@ -48,6 +48,8 @@ _SIGS = {
     "rq_tuxv_iter": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
     "rq_rsrqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, ctypes.c_uint64, _P, _P, _P, _P], _I),
+    "rq_latent_cdf": ([_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], _I),
+    "rq_padding": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], _I),
     "rq_gaussian": ([_P, _I, ctypes.c_uint64, ctypes.c_uint64, _I, _I, _P, _I, _P], _I),
 }
 
@@ -176,6 +178,24 @@ def rq_rsrqrcp(h, prec, m, n, A, lda, b, p, k, seed, tau, jpvt, info, stream=Non
 def rq_gaussian(h, prec, seed, substream, l, m, Omega, ldo, stream=None):
     return load().rq_gaussian(h, prec, seed & 0xFFFFFFFFFFFFFFFF, substream & 0xFFFFFFFFFFFFFFFF, l, m, _ptr(Omega),
                               ldo, _stream(stream))
+
+
+def rq_latent_cdf(l, tau):
+    """P(phi < tau | l) of the sample's posterior (Sec. 3.3), computed by the library."""
+    out = ctypes.c_double()
+    rc = load().rq_latent_cdf(l, tau, ctypes.byref(out))
+    if rc != RQ_OK:
+        raise ValueError(f"rq_latent_cdf({l}, {tau}) failed with status {rc}")
+    return out.value
+
+
+def rq_padding(tau, delta):
+    """Smallest padding p keeping every pivot decision's P(phi < tau) <= delta."""
+    out = ctypes.c_int()
+    rc = load().rq_padding(tau, delta, ctypes.byref(out))
+    if rc != RQ_OK:
+        raise ValueError(f"rq_padding({tau}, {delta}) failed with status {rc}")
+    return out.value
 
 
 def rq_qr(h, prec, m, n, A, lda, b, tau, info, stream=None):

@@ -80,3 +80,20 @@ def test_trqrcp_equals_gpu_rqrcp(H):
     F = to_host(A)
     assert np.array_equal(jpvt, jp2.cpu().numpy())
     assert np.max(np.abs(R - np.triu(F[:k]))) <= 1e-12 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("m,n,k,b,p", [(500, 300, 24, 24, 8), (400, 350, 10, 32, 8), (90, 70, 1, 16, 4)])
+def test_single_sample_case_is_alg3(H, m, n, k, b, p):
+    """k <= b: one sample, one panel, no update (the single-sample algorithm,
+    Alg. 3): R = Q(:, 1:k)^T A P to 1e-12 ||A||_F, with the oracle's pivots."""
+    a = I.graded(m, n, 8, seed=m + k)
+    om = I.omega(b + p, m, seed=k + 3)
+    Y, tau, R, jpvt, info = run_gpu(H, a, om, b, p, k)
+    T = O.larft(Y, tau)
+    Qk = (np.eye(m) - Y @ T @ Y.T)[:, :k]
+    nrm = np.linalg.norm(a)
+    assert np.max(np.abs(Qk.T @ a[:, jpvt] - R)) <= 1e-12 * nrm
+    ref = O.trqrcp(a, om, b, k)
+    tie = first_near_tie(ref.gaps, b, TIE)
+    upto = k if tie is None else tie
+    assert np.array_equal(jpvt[:upto], ref.jpvt[:upto])
