@@ -49,9 +49,82 @@ def parse():
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched leg")
+    ap.add_argument("--sweep", default="", help="paper-shaped timing sweeps instead of the bench line (comma list of "
+                    + ", ".join(SWEEPS) + ", or 'all'); one JSON line per point")
     args = ap.parse_args()
     args.legs = set() if args.no_extras else {x.strip() for x in args.legs.split(",") if x.strip()}
     return args
+
+
+# Paper-shaped timing sweeps (Sec. 5.1 full decompositions, Sec. 5.2 truncated):
+# (m, n, k) per point, k = None for a full factorisation.  The paper scales
+# around 12000 x 12000 with truncation rank 1200.
+SWEEPS = {
+    "full-order": [(n, n, None) for n in (2000, 4000, 6000, 8000, 10000, 12000)],
+    "full-cols": [(12000, n, None) for n in (3000, 6000, 12000, 24000)],
+    "full-rows": [(m, 12000, None) for m in (3000, 6000, 12000, 24000)],
+    "trunc-rank": [(12000, 12000, k) for k in (150, 300, 600, 1200, 2400)],
+    "trunc-cols": [(12000, n, 1200) for n in (3000, 6000, 12000, 24000)],
+    "trunc-rows": [(m, 12000, 1200) for m in (3000, 6000, 12000, 24000)],
+}
+
+
+def run_sweep(args):
+    """Times each algorithm once (after one untimed call at the same size) on an
+    i.i.d. Gaussian matrix (the paper's timing matrices are random), FP64 unless
+    --prec fp32.  Full points: RQRCP, RSRQRCP, unpivoted QR, and cuSOLVER geqrf
+    through torch as context.  Truncated points: RQRCP, RSRQRCP (both with the
+    trailing update, halted at k), TRQRCP and TUXV (j_max = 1)."""
+    import torch
+    from paper_2008_04447_gb300 import Handle, build as B
+    B.build()
+    names = list(SWEEPS) if args.sweep == "all" else [x.strip() for x in args.sweep.split(",") if x.strip()]
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    h = Handle()
+    b, p = args.b, args.p
+    l = b + p
+    gen = torch.Generator(device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(prep, run):
+        out = []
+        for _ in range(2):
+            prep()
+            torch.cuda.synchronize()
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) / 1e3)
+        return out[-1]
+
+    for name in names:
+        for (m, n, k) in SWEEPS[name]:
+            gen.manual_seed(m * 100003 + n)
+            A0 = torch.randn((n, m), generator=gen, device="cuda", dtype=dt).t()    # column-major m x n
+            A = torch.empty_like(A0.t()).t()
+            Om = h.gaussian(l, m, 1, dtype=dt)
+            kk = min(m, n) if k is None else k
+            res = {}
+
+            def restore():
+                A.copy_(A0)
+            res["rqrcp"] = timed(restore, lambda: h.rqrcp(A, Om, b, p, kk))
+            res["rsrqrcp"] = timed(restore, lambda: h.rsrqrcp(A, 7, b, p, kk))
+            if k is None:
+                res["qr"] = timed(restore, lambda: h.qr(A, b))
+                res["cusolver_geqrf_via_torch"] = timed(restore, lambda: torch.geqrf(A))
+            else:
+                res["trqrcp"] = timed(lambda: None, lambda: h.trqrcp(A0, Om, b, p, kk))
+                res["tuxv"] = timed(lambda: None, lambda: h.tuxv(A0, Om, b, p, kk))
+            fl = flops_qr(m, n) if k is None else 4.0 * m * n * kk - 2.0 * (m + n) * kk * kk + 4.0 * kk ** 3 / 3.0
+            line = {"sweep": name, "m": m, "n": n, "k": kk, "b": b, "p": p, "dtype": args.prec, "data": "synthetic",
+                    "matrix": "i.i.d. N(0,1)", "seconds": res,
+                    "tflops_householder_count": {a: fl / t / 1e12 for a, t in res.items()}}
+            print(json.dumps(line), flush=True)
+            del A0, A
+            torch.cuda.empty_cache()
 
 
 def flops_qr(m, n):
@@ -360,6 +433,9 @@ def run_reference(args, ws, rank):
 
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
