@@ -47,8 +47,11 @@ def parse():
                     help="extra legs to run (comma list); --no-extras clears it")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the timed RQRCP")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
+    ap.add_argument("--only", default="", choices=["", "tuxv", "batched"],
+                    help="run only this leg and print its JSON (profiling)")
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched leg")
+    ap.add_argument("--tuxv-shape", default="32768,16384,512", help="m,n,k of the TUXV leg")
     ap.add_argument("--sweep", default="", help="paper-shaped timing sweeps instead of the bench line (comma list of "
                     + ", ".join(SWEEPS) + ", or 'all'); one JSON line per point")
     args = ap.parse_args()
@@ -287,12 +290,14 @@ def leg_rsrqrcp(h, A0, A, Om, b, p, fl, rqrcp_ms, prec):
     return out
 
 
-def leg_tuxv(h, steps=3, warmup=3):
-    """Truncated RQRCP + TUXV of one 32768 x 16384 matrix (low rank + noise), k = 512."""
+def leg_tuxv(h, steps=3, warmup=3, shape=(32768, 16384, 512)):
+    """Truncated RQRCP + TUXV of one m x n matrix (low rank + noise; default
+    32768 x 16384, k = 512), mixed precision."""
     import torch
     from paper_2008_04447_gb300 import RQ_MIXED, colmajor
     from paper_2008_04447_gb300 import inputs as I
-    m, n, k, b, p = 32768, 16384, 512, 64, 8
+    m, n, k = shape
+    b, p = 64, 8
     A = colmajor(I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7).float())
     Om = colmajor(I.omega_torch(b + p, m, seed=8, dtype=torch.float32))
     for _ in range(warmup):
@@ -447,9 +452,13 @@ def main():
     if rank == 0:
         B.build()
     barrier(ws)
-    if args.only_batched:
+    if args.only_batched or args.only == "batched":
         host = batch_inputs(args.batch, seed=0)
         print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), oracle_sample=0)}), flush=True)
+        return
+    if args.only == "tuxv":
+        shape = tuple(int(x) for x in args.tuxv_shape.split(","))
+        print(json.dumps({"tuxv": leg_tuxv(Handle(), steps=args.steps, warmup=args.warmup, shape=shape)}), flush=True)
         return
     n, b, p = args.n, args.b, args.p
     m = n

@@ -12,45 +12,89 @@ namespace rq {
 // (about one to two seconds).  A wait that runs out sets RQ_ETIMEOUT in the
 // error word and returns, so the kernel ends instead of hanging the GPU.
 constexpr long long kSpinLimit = 1ll << 24;
+// Polls of a grid barrier's generation word before it gives up (each poll is
+// an L2 round trip, with a 32 ns sleep after the first 256): about a second.
+constexpr long long kGridWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).
-// bar[0] = arrival count, bar[1] = generation.  Must start at {0, g}.
-// Returns false when the error word is (or becomes) set; callers then return.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) {
+// bar[0] counts the arrivals since the kernel began and bar[1] the CTAs that
+// have left; both are 0 when a kernel starts, and grid_exit puts them back to
+// 0 when the last CTA leaves, for the next launch on the stream.  Every CTA
+// counts its barriers in `epoch` (the same value in all its threads); barrier
+// e is complete when bar[0] reaches (e + 1) G.  Thread 0 adds its arrival with
+// release order after the CTA's bar.sync (publishing every thread's earlier
+// writes) and polls with acquire loads: one L2 round trip each way.  The
+// arrive and the wait are separate so that a CTA can work in between.
+// Cross-CTA data written before a barrier is read after it through L2 (__ldcg).
+__device__ __forceinline__ void grid_arrive(unsigned int* bar) {
   __syncthreads();
+  if (threadIdx.x == 0) red_add_release_gpu(bar, 1u);
+}
+
+// Returns false when the error word is (or becomes) set or the wait runs out
+// (then RQ_ETIMEOUT is recorded); callers then return.
+__device__ __forceinline__ bool grid_wait(unsigned int* bar, unsigned int nblocks, int* err, unsigned int epoch) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int* vgen = bar + 1;
-    volatile int* verr = err;
-    if (*verr != 0) {
-      ok = 0;
-    } else {
-      unsigned int gen = *vgen;
-      __threadfence();
-      unsigned int arrived = atomicAdd(bar, 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
-      } else {
-        long long it = 0;
-        while (*vgen == gen) {
-          if (*verr != 0) { ok = 0; break; }
-          if (++it > kSpinLimit) {
-            atomicCAS(err, 0, RQ_ETIMEOUT);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
+    const unsigned int target = (epoch + 1u) * nblocks;
+    long long it = 0;
+    while (static_cast<int>(ld_acquire_gpu(bar) - target) < 0) {
+      ++it;
+      if ((it & 63) == 0) {
+        if (*reinterpret_cast<volatile int*>(err) != 0) { ok = 0; break; }
+        if (it > kGridWaitLimit) {
+          atomicCAS(err, 0, RQ_ETIMEOUT);
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
+      if (it > 256) __nanosleep(32);
     }
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err, unsigned int& epoch) {
+  grid_arrive(bar);
+  const bool ok = grid_wait(bar, nblocks, err, epoch);
+  ++epoch;
+  return ok;
+}
+
+// Every CTA calls this last (after its final barrier); the last one to leave
+// returns both counters to 0.
+__device__ __forceinline__ void grid_exit(unsigned int* bar, unsigned int nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int old = atom_add_acq_rel_gpu(bar + 1, 1u);
+    if (old == nblocks - 1) {
+      st_relaxed_gpu(bar, 0u);
+      st_relaxed_gpu(bar + 1, 0u);
+    }
+  }
 }
 
 template <typename T>

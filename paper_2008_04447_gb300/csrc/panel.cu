@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
   for (int e = tid; e < bj * bj; e += kThreads) Tm[e] = 0.0;
   __syncthreads();
 
+  unsigned int epoch = 0;
   for (int j = 0; j < bj; ++j) {
     const int par = j & 1;
     double* part = a.part + (size_t)par * G * recn;
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
         rowb[bj + c] = (c < j) ? static_cast<double>(p[(size_t)c * rpc + jl]) : 0.0;
       }
     }
-    if (!grid_barrier(a.bar, G, a.err)) return;
+    if (!grid_barrier(a.bar, G, a.err, epoch)) return;
     // reduce the partials in a fixed order (CTA 0 also needs the e_i)
     const int need = (cta == 0) ? bj : (bj - j);
     for (int t = lane; t < need; t += 32) {
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
     __syncthreads();
   }
 
+  grid_exit(a.bar, G);
   for (int e = tid; e < nr * bj; e += kThreads) {
     const int r = e % nr, c = e / nr;
     const int g = r0 + r;
@@ -203,6 +205,258 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
   }
   if (cta == 0)
     for (int e = tid; e < bj * bj; e += kThreads) a.T[(size_t)(e / bj) * a.ldt + (e % bj)] = Tm[e];
+}
+
+// ---------------------------------------------------------------------------
+// Latency-oriented variant for b <= 64 (the common case): the per-column step
+// is a chain of waits (a grid barrier, reductions, one FP64 square root and
+// division), so it is shaped to keep that chain short.
+//   * Each thread owns one row of the panel (two threads split a row's 64
+//     columns in FP64) and keeps it in registers; reflector j-1 is applied to
+//     the row's columns >= j with no barrier inside the CTA.
+//   * Finished columns stay unscaled in the registers: y_c(g) = a_c(g) / y1_c,
+//     and every use (the e_i sums, T, the outputs) applies 1 / y1_c.
+//   * The row's products a_c(g) a_j(g) for all c are reduced over the warp at
+//     once by a reduce-scatter butterfly (62 shuffles for 64 sums), then over
+//     the warps through shared memory; the squared norm is summed in FP64.
+//   * CTA 0 forms T's previous column between its arrival at the grid barrier
+//     and its wait, off the critical path.
+//   * tau = (beta - alpha) / beta and 1 / y1 come from one FP64 division,
+//     1 / (beta y1); tau = 2 exactly when the column is zero below row j.
+// The squared norm, beta, tau, 1 / y1 and T are FP64; the lazy update, the
+// products and their reductions run in the storage precision, like the
+// general kernel above.
+constexpr int kFB = 64;
+constexpr int kMaxG4 = 40;  // partial records per thread in the sums: G <= 160
+
+template <typename TS>
+struct FastArgs {
+  TS* P;
+  int ldp, mt, bj;
+  TS* tau;
+  TS* Y;
+  int ldy;
+  double* T;
+  int ldt;
+  TS* part;        // 2 * G * bj partial sums
+  double* x2part;  // 2 * G partial squared norms
+  TS* rowb;        // 2 * bj: row j of the panel
+  unsigned int* bar;
+  int* err;
+  int rpc;
+};
+
+// v[0..N) per lane, LPG lanes per group (N = 2 LPG): afterwards lane l of the
+// group holds in v[0], v[1] the group sums of values 2l and 2l + 1.
+template <typename T, int N, int LPG>
+__device__ __forceinline__ void reduce_scatter(T (&v)[N]) {
+  static_assert(N == 2 * LPG, "two sums per lane");
+#pragma unroll
+  for (int lev = 0; (LPG >> (lev + 1)) >= 1; ++lev) {
+    const int off = LPG >> (lev + 1);
+    const int n = N >> lev;
+    const bool up = (threadIdx.x & off) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const T send = up ? v[i] : v[i + n / 2];
+      const T keep = up ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+// T(0:jc, jc) = -tau T(0:jc, 0:jc) tv, T(jc, jc) = tau (compound WY, Sec. 4.1);
+// four threads per entry, fixed order.
+__device__ __forceinline__ void t_column(int jc, double tau, double* sT, const double* tv) {
+  const int i = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  double acc = 0.0;
+  if (i < jc)
+    for (int q = i + sub; q < jc; q += 4) acc = fma(sT[(size_t)q * kFB + i], tv[q], acc);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (sub == 0 && i < jc) sT[(size_t)jc * kFB + i] = -tau * acc;
+  if (threadIdx.x == 0) sT[(size_t)jc * kFB + jc] = tau;
+}
+
+template <typename TS, int TPR>
+__global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a) {
+  constexpr int CPT = kFB / TPR;  // columns per thread
+  constexpr int LPG = 32 / TPR;   // lanes (rows) per group of a warp
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int bj = a.bj;
+  const int half = lane / LPG;
+  const int lp = lane % LPG;
+  const int r = warp * LPG + lp;
+  const int g = cta * a.rpc + r;
+  const bool live = r < a.rpc && g < a.mt;
+  const int cbase = half * CPT;
+  __shared__ TS s_tw[kFB];
+  __shared__ double s_sum[kFB];
+  __shared__ double s_row[kFB];
+  __shared__ double s_inv[kFB];
+  __shared__ double s_beta[kFB];
+  __shared__ double s_tv[kFB];
+  __shared__ double s_T[kFB * kFB];
+  __shared__ TS s_red[kWarps][kFB];
+  __shared__ double s_redx[kWarps];
+  __shared__ double s_sc[4];
+
+  TS row[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int c = cbase + q;
+    row[q] = (live && c < bj) ? a.P[(size_t)g + (size_t)c * a.ldp] : TS(0);
+  }
+  if (cta == 0)
+    for (int e = tid; e < kFB * kFB; e += kThreads) s_T[e] = 0.0;
+  TS vprev = TS(0);
+
+  for (int j = 0; j < bj; ++j) {
+    const int par = j & 1;
+    TS* part = a.part + (size_t)par * G * bj;
+    double* x2p = a.x2part + (size_t)par * G;
+    TS* rowb = a.rowb + (size_t)par * bj;
+    // (1) reflector j-1 on this row's columns >= j; pick up a_j(g)
+    TS aj = TS(0);
+    const bool upd = j > 0 && live && g >= j - 1;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int c = cbase + q;
+      if (upd && c >= j && c < bj) row[q] = fma(-s_tw[c], vprev, row[q]);
+      if (c == j) aj = row[q];
+    }
+    if (TPR == 2) {
+      const TS o = __shfl_xor_sync(0xffffffffu, aj, 16);
+      if (half != j / CPT) aj = o;
+    }
+    if (live && g == j) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q)
+        if (cbase + q < bj) rowb[cbase + q] = row[q];
+    }
+    // (2) this row's share of the sums over rows g > j, reduced over the CTA
+    const bool below = live && g > j;
+    TS prod[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int c = cbase + q;
+      prod[q] = (below && c != j && c < bj) ? row[q] * aj : TS(0);
+    }
+    double x2 = (below && half == j / CPT) ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
+    reduce_scatter<TS, CPT, LPG>(prod);
+    x2 = warp_sum(x2);
+    s_red[warp][cbase + 2 * lp] = prod[0];
+    s_red[warp][cbase + 2 * lp + 1] = prod[1];
+    if (lane == 0) s_redx[warp] = x2;
+    __syncthreads();
+    if (tid < bj) {
+      TS acc = TS(0);
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) acc += s_red[w][tid];
+      part[(size_t)cta * bj + tid] = acc;
+    } else if (tid == kFB) {
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) acc += s_redx[w];
+      x2p[cta] = acc;
+    }
+    // (3) grid barrier; CTA 0 completes T's previous column meanwhile
+    grid_arrive(a.bar);
+    if (cta == 0 && j > 0) t_column(j - 1, s_sc[3], s_T, s_tv);
+    if (!grid_wait(a.bar, G, a.err, static_cast<unsigned int>(j))) return;
+    // (4) global sums in a fixed order (identical on every CTA), four threads
+    // per value, every load in flight at once; CTA 0 also needs the columns < j
+    // for T.  The thread that completes the squared norm goes straight on to
+    // reflector j's FP64 scalars while the other sums finish.
+    {
+      const int v = tid >> 2, sub = tid & 3;
+      const bool want = v < bj && (v >= j || cta == 0);
+      double acc = 0.0;
+      double alpha = 0.0;
+      if (want && v == j) {
+        alpha = static_cast<double>(__ldcg(rowb + j));
+        double x[kMaxG4];
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) {
+          const int q = sub + 4 * u;
+          x[u] = q < G ? __ldcg(x2p + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) acc += x[u];
+      } else if (want) {
+        TS x[kMaxG4];
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) {
+          const int q = sub + 4 * u;
+          x[u] = q < G ? __ldcg(part + (size_t)q * bj + v) : TS(0);
+        }
+        TS t = TS(0);
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) t += x[u];
+        acc = static_cast<double>(t);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (sub == 0 && v < bj) s_sum[v] = acc;
+      if (sub == 0 && v == j) {
+        // (5) reflector j (FP64): beta = -sign(alpha) ||a||, y1 = alpha - beta,
+        // 1 / y1 and tau = (beta - alpha) / beta from one division
+        const double x2s = acc;
+        const double nrm2 = fma(alpha, alpha, x2s);
+        double tau = 0.0, beta = 0.0, inv = 0.0;
+        if (nrm2 > 0.0) {
+          const double nrm = sqrt(nrm2);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          const double y1 = alpha - beta;
+          const double rr = 1.0 / (beta * y1);
+          inv = beta * rr;
+          tau = x2s == 0.0 ? 2.0 : -y1 * (y1 * rr);
+        }
+        s_sc[0] = tau;
+        s_sc[1] = inv;
+        s_inv[j] = inv;
+        s_beta[j] = beta;
+        if (cta == 0) a.tau[j] = static_cast<TS>(tau);
+      }
+    }
+    if (tid < bj) s_row[tid] = static_cast<double>(__ldcg(rowb + tid));
+    __syncthreads();
+    const double tau = s_sc[0], inv = s_sc[1];
+    if (tid > j && tid < bj) s_tw[tid] = static_cast<TS>(tau * fma(s_sum[tid], inv, s_row[tid]));
+    if (cta == 0 && tid < j) s_tv[tid] = s_inv[tid] * fma(s_sum[tid], inv, s_row[tid]);
+    if (cta == 0 && tid == 0) s_sc[3] = tau;
+    vprev = !live ? TS(0) : (g > j ? static_cast<TS>(static_cast<double>(aj) * inv) : (g == j ? TS(1) : TS(0)));
+    __syncthreads();
+  }
+  grid_exit(a.bar, G);
+  if (cta == 0) {
+    t_column(bj - 1, s_sc[3], s_T, s_tv);
+    __syncthreads();
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int c = cbase + q;
+      if (c >= bj) continue;
+      TS op, oy;
+      if (g > c) {
+        op = static_cast<TS>(static_cast<double>(row[q]) * s_inv[c]);
+        oy = op;
+      } else if (g == c) {
+        op = static_cast<TS>(s_beta[c]);
+        oy = TS(1);
+      } else {
+        op = row[q];
+        oy = TS(0);
+      }
+      a.P[(size_t)g + (size_t)c * a.ldp] = op;
+      a.Y[(size_t)g + (size_t)c * a.ldy] = oy;
+    }
+  }
+  if (cta == 0)
+    for (int e = tid; e < bj * bj; e += kThreads)
+      a.T[(size_t)(e / bj) * a.ldt + (e % bj)] = s_T[(size_t)(e / bj) * kFB + (e % bj)];
 }
 
 template <typename TS>
@@ -221,6 +475,32 @@ template <typename TS>
 cudaError_t panel_qr(const Ctx& c, TS* P, int ldp, int mt, int bj, TS* tau, TS* Y, int ldy,
                      double* T, int ldt, double* scratch) {
   if (bj > kMaxB || bj > mt || bj < 1) return cudaErrorInvalidValue;
+  {
+    // the thread-per-row kernel when the panel fits one row per thread
+    constexpr int TPR = sizeof(TS) == sizeof(double) ? 2 : 1;
+    constexpr int RPP = kThreads / TPR;
+    const int Gf = (mt + RPP - 1) / RPP;
+    if (bj <= kFB && Gf <= c.num_sms && Gf <= 4 * kMaxG4) {
+      static int per_sm_fast = -1;
+      if (per_sm_fast < 0) {
+        cudaError_t eo = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_fast, panel_fast_kernel<TS, TPR>,
+                                                                       kThreads, 0);
+        if (eo != cudaSuccess) return eo;
+      }
+      if (per_sm_fast * c.num_sms >= Gf) {
+        const int rpc = (mt + Gf - 1) / Gf;
+        TS* part = reinterpret_cast<TS*>(scratch);
+        double* x2part = scratch + 2 * (size_t)Gf * bj;
+        TS* rowb = reinterpret_cast<TS*>(x2part + 2 * (size_t)Gf);
+        FastArgs<TS> fa{P, ldp, mt, bj, tau, Y, ldy, T, ldt, part, x2part, rowb, c.bar, c.err, rpc};
+        void* fargs[] = {&fa};
+        cudaError_t ef = cudaLaunchCooperativeKernel((const void*)panel_fast_kernel<TS, TPR>, dim3(Gf),
+                                                     dim3(kThreads), fargs, 0, c.stream);
+        ++*c.launches;
+        return ef;
+      }
+    }
+  }
   int G = (mt + 31) / 32;
   if (G > c.num_sms) G = c.num_sms;
   if (G > kMaxRec * kWarps) G = kMaxRec * kWarps;

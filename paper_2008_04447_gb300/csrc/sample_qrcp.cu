@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
   }
   __syncthreads();
 
+  unsigned int epoch = 0;
   for (int i = 0; i < steps; ++i) {
     const int par = i & 1;
     double* tab = a.cand + (size_t)par * G * rec;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
         for (int r = tid; r < l; r += kThreads) tab[(size_t)cta * rec + 2 + r] = static_cast<double>(s[(size_t)r * cpc + lc]);
     }
     // (2)
-    if (!grid_barrier(a.bar, G, a.err)) return;
+    if (!grid_barrier(a.bar, G, a.err, epoch)) return;
     // (3) global winner: same reduction order on every CTA
     if (warp == 0) {
       double gv = -1.0;
@@ -161,12 +162,12 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
       x2 = warp_sum(x2);
       const double alpha = wcol[i];
       const double nrm2 = fma(alpha, alpha, x2);
-      double beta = 0.0, y1 = 1.0;
+      double beta = 0.0, inv = 0.0;
       const bool zero = !(nrm2 > 0.0);
       if (!zero) {
         const double nrm = sqrt(nrm2);
         beta = alpha >= 0.0 ? -nrm : nrm;
-        y1 = alpha - beta;
+        inv = 1.0 / (alpha - beta);
       }
       if (cta == 0) {
         double* col = a.S11 + (size_t)i * a.lds;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
         TS v;
         if (r < i) v = TS(0);
         else if (r == i) v = TS(1);
-        else v = zero ? TS(0) : static_cast<TS>(wcol[r] / y1);
+        else v = static_cast<TS>(wcol[r] * inv);
         vv[r] = v;
         if (r > i) v2 = fma(static_cast<double>(v), static_cast<double>(v), v2);
       }
@@ -190,8 +191,17 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     for (int c = tid; c < nc; c += kThreads) {
       if (!alive[c]) continue;
       if (tau != TS(0)) {
-        TS w = s[(size_t)i * cpc + c];
-        for (int r = i + 1; r < l; ++r) w = fma(vv[r], s[(size_t)r * cpc + c], w);
+        // w = v^T s_c with four partial sums (a short dependency chain)
+        TS w0 = s[(size_t)i * cpc + c], w1 = TS(0), w2 = TS(0), w3 = TS(0);
+        int r = i + 1;
+        for (; r + 3 < l; r += 4) {
+          w0 = fma(vv[r], s[(size_t)r * cpc + c], w0);
+          w1 = fma(vv[r + 1], s[(size_t)(r + 1) * cpc + c], w1);
+          w2 = fma(vv[r + 2], s[(size_t)(r + 2) * cpc + c], w2);
+          w3 = fma(vv[r + 3], s[(size_t)(r + 3) * cpc + c], w3);
+        }
+        for (; r < l; ++r) w0 = fma(vv[r], s[(size_t)r * cpc + c], w0);
+        const TS w = (w0 + w1) + (w2 + w3);
         const TS tw = tau * w;
         s[(size_t)i * cpc + c] -= tw;
         for (int r = i + 1; r < l; ++r) s[(size_t)r * cpc + c] = fma(-tw, vv[r], s[(size_t)r * cpc + c]);
@@ -199,11 +209,19 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
       const double x = static_cast<double>(s[(size_t)i * cpc + c]);
       double nn = nu2[c] - x * x;
       if (nn <= tol * ref2[c]) {
-        nn = 0.0;
-        for (int r = i + 1; r < l; ++r) {
-          const double y = static_cast<double>(s[(size_t)r * cpc + c]);
-          nn = fma(y, y, nn);
+        double n0 = 0.0, n1 = 0.0;
+        int r = i + 1;
+        for (; r + 1 < l; r += 2) {
+          const double y0 = static_cast<double>(s[(size_t)r * cpc + c]);
+          const double y1 = static_cast<double>(s[(size_t)(r + 1) * cpc + c]);
+          n0 = fma(y0, y0, n0);
+          n1 = fma(y1, y1, n1);
         }
+        if (r < l) {
+          const double y0 = static_cast<double>(s[(size_t)r * cpc + c]);
+          n0 = fma(y0, y0, n0);
+        }
+        nn = n0 + n1;
         ref2[c] = nn;
       }
       nu2[c] = nn;
@@ -211,6 +229,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     __syncthreads();
   }
 
+  grid_exit(a.bar, G);
   // outputs: new order of the columns, the reordered trailing sample
   for (int c = tid; c < nc; c += kThreads) a.src[pos[c]] = c0 + c;
   for (int e = tid; e < l * nc; e += kThreads) {

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kJThreads) jacobi_kernel(JacArgs a) {
   __shared__ double s_c, s_s;
   __shared__ int s_go;
   const int G = gridDim.x, k = a.k, kk = a.kk, npairs = kk / 2;
+  unsigned int epoch = 0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     for (int r = 0; r < kk - 1; ++r) {
       for (int pi = blockIdx.x; pi < npairs; pi += G) {
@@ -135,13 +136,14 @@ __global__ void __launch_bounds__(kJThreads) jacobi_kernel(JacArgs a) {
         }
         __syncthreads();
       }
-      if (!grid_barrier(a.bar, G, a.err)) return;
+      if (!grid_barrier(a.bar, G, a.err, epoch)) return;
     }
     __shared__ int s_count;
     if (threadIdx.x == 0) s_count = __ldcg(a.rot + sweep);
     __syncthreads();
-    if (s_count == 0) return;
+    if (s_count == 0) break;
   }
+  grid_exit(a.bar, G);
 }
 
 // nrm_j = ||W(:, j)||
