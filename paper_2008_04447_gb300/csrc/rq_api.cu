@@ -495,8 +495,8 @@ cudaError_t qr_explicit(const Ctx& c, TS* M, int ldm, int rows, int k, int b, co
     }
     TS* M2 = M + j0 + (size_t)(j0 + bj) * ldm;
     if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), Yj, rows, Tm, b, TS(0), s.YT, mt);
-    if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, n2, mt, TS(1), s.YT, mt, M2, ldm, TS(0), s.Wt, b);
-    if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, n2, bj, TS(-1), Yj, rows, s.Wt, b, TS(1), M2, ldm);
+    if (e == cudaSuccess) e = prod_tn_skinny<TS>(c, bj, n2, mt, s.YT, mt, M2, ldm, s.Wt, b);
+    if (e == cudaSuccess) e = prod_nn<TS>(c, mt, n2, bj, TS(-1), Yj, rows, s.Wt, b, TS(1), M2, ldm);
   }
   if (e == cudaSuccess && Rout) e = copy_upper<TS>(c, k, M, ldm, Rout, ldr);
   if (e == cudaSuccess) e = set_eye<TS>(c, rows, k, Q, ldq);
@@ -511,9 +511,9 @@ cudaError_t qr_explicit(const Ctx& c, TS* M, int ldm, int rows, int k, int b, co
     }
     TS* Qs = Q + j0 + (size_t)j0 * ldq;
     // Qs <- (I - Y T Y^T) Qs
-    if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, nc, mt, TS(1), Yj, rows, Qs, ldq, TS(0), s.Wt, b);
+    if (e == cudaSuccess) e = prod_tn_skinny<TS>(c, bj, nc, mt, Yj, rows, Qs, ldq, s.Wt, b);
     if (e == cudaSuccess) e = gemm<TS>(c, false, false, bj, nc, bj, TS(1), Tm, b, s.Wt, b, TS(0), s.YT, b);
-    if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, nc, bj, TS(-1), Yj, rows, s.YT, b, TS(1), Qs, ldq);
+    if (e == cudaSuccess) e = prod_nn<TS>(c, mt, nc, bj, TS(-1), Yj, rows, s.YT, b, TS(1), Qs, ldq);
   }
   return e;
 }

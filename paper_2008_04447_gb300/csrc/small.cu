@@ -142,6 +142,73 @@ __global__ void sample_update_idx_kernel(int bj, int n2, const double* __restric
   }
 }
 
+// Omegahat_11 = S11 R11^{-1} for b <= 64 by forward substitution along each
+// row, Oh(r, j) = (S11(r, j) - sum_{i<j} Oh(r, i) R11(i, j)) / R11(j, j), all
+// rows at once, four threads per row (partial sums over i = sub mod 4, in a
+// fixed order), the rows kept in shared memory.
+template <typename TS>
+__global__ void omegahat_fast_kernel(const double* __restrict__ S11, int lds, const TS* __restrict__ R11, int ldr,
+                                     int bj, double* __restrict__ Oh, int ldo) {
+  extern __shared__ double so[];
+  double* sR = so;                   // bj x bj, column-major, upper
+  double* sX = sR + (size_t)bj * bj;  // sX[r + i * bj] = Oh(r, i)
+  double* sInv = sX + (size_t)bj * bj;
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) {
+    const int i = e % bj, j = e / bj;
+    sR[e] = i <= j ? static_cast<double>(R11[i + (size_t)j * ldr]) : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < bj; j += blockDim.x) {
+    const double d = sR[j + (size_t)j * bj];
+    sInv[j] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  for (int j = 0; j < bj; ++j) {
+    double acc = 0.0;
+    if (r < bj)
+      for (int i = r + sub; i < j; i += 4) acc = fma(sX[r + (size_t)i * bj], sR[i + (size_t)j * bj], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (r < bj && sub == 0) sX[r + (size_t)j * bj] = j < r ? 0.0 : (S11[r + (size_t)j * lds] - acc) * sInv[j];
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) Oh[(e % bj) + (size_t)(e / bj) * ldo] = sX[e];
+}
+
+// B1(:, t) -= Oh R12(:, t), R12(:, t) = Zb(:, idx[t]), for b <= 64: one CTA per
+// 64 columns, Oh and the gathered R12 tile in shared memory; each entry
+// accumulates over i = r .. b-1 in order, in the storage precision.
+template <typename TS>
+__global__ void __launch_bounds__(256) sample_update_tile_kernel(int bj, int n2, const double* __restrict__ Oh,
+                                                                 int ldo, const TS* __restrict__ Zb, int ldz,
+                                                                 const int* __restrict__ idx, TS* __restrict__ B1,
+                                                                 int ldb) {
+  extern __shared__ __align__(16) unsigned char su_raw[];
+  TS* sO = reinterpret_cast<TS*>(su_raw);  // sO[r * 64 + i]
+  TS* sZ = sO + 64 * 64;                   // sZ[i * 65 + cc]
+  const int tid = threadIdx.x, col0 = blockIdx.x * 64;
+  for (int e = tid; e < bj * bj; e += 256) {
+    const int r = e % bj, i = e / bj;
+    sO[r * 64 + i] = static_cast<TS>(Oh[r + (size_t)i * ldo]);
+  }
+  for (int e = tid; e < bj * 64; e += 256) {
+    const int i = e % bj, cc = e / bj, col = col0 + cc;
+    sZ[i * 65 + cc] = col < n2 ? Zb[i + (size_t)idx[col] * ldz] : TS(0);
+  }
+  __syncthreads();
+  const int cc = tid & 63, rg = tid >> 6, col = col0 + cc;
+  if (col >= n2) return;
+  for (int rr = 0; rr < 16; ++rr) {
+    const int r = rg * 16 + rr;
+    if (r >= bj) break;
+    TS acc = TS(0);
+    for (int i = r; i < bj; ++i) acc = fma(sO[r * 64 + i], sZ[i * 65 + cc], acc);
+    B1[r + (size_t)col * ldb] -= acc;
+  }
+}
+
 __global__ void iota_kernel(int* v, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
 }
@@ -190,9 +257,22 @@ cudaError_t permute_columns(const Ctx& c, TS* A, int lda, int m, int steps, cons
 template <typename TS>
 cudaError_t omegahat11(const Ctx& c, const double* S11, int lds, const TS* R11, int ldr, int bj, double* Oh,
                        int ldo) {
-  const int threads = bj <= 32 ? 32 : (bj <= 64 ? 64 : (bj <= 128 ? 128 : 256));
-  omegahat_kernel<TS><<<(bj + threads - 1) / threads, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(
-      S11, lds, R11, ldr, bj, Oh, ldo);
+  if (bj <= 64) {
+    const size_t smem = (2 * (size_t)bj * bj + bj) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t ea = cudaFuncSetAttribute(omegahat_fast_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)((2 * 64 * 64 + 64) * sizeof(double)));
+      if (ea != cudaSuccess) return ea;
+      attr = true;
+    }
+    const int threads = (4 * bj + 31) / 32 * 32;
+    omegahat_fast_kernel<TS><<<1, threads, smem, c.stream>>>(S11, lds, R11, ldr, bj, Oh, ldo);
+  } else {
+    const int threads = bj <= 128 ? 128 : 256;
+    omegahat_kernel<TS><<<(bj + threads - 1) / threads, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(
+        S11, lds, R11, ldr, bj, Oh, ldo);
+  }
   ++*c.launches;
   return cudaGetLastError();
 }
@@ -240,9 +320,21 @@ template <typename TS>
 cudaError_t sample_update_idx(const Ctx& c, int bj, int n2, const double* Oh, int ldo, const TS* Zb, int ldz,
                               const int* idx, TS* B1, int ldb) {
   if (n2 <= 0) return cudaSuccess;
-  const int threads = bj <= 32 ? 32 : (bj <= 64 ? 64 : (bj <= 128 ? 128 : 256));
-  sample_update_idx_kernel<TS><<<n2, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(bj, n2, Oh, ldo, Zb,
-                                                                                             ldz, idx, B1, ldb);
+  if (bj <= 64) {
+    const size_t smem = (64 * 64 + 64 * 65) * sizeof(TS);
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t ea =
+          cudaFuncSetAttribute(sample_update_tile_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (ea != cudaSuccess) return ea;
+      attr = true;
+    }
+    sample_update_tile_kernel<TS><<<(n2 + 63) / 64, 256, smem, c.stream>>>(bj, n2, Oh, ldo, Zb, ldz, idx, B1, ldb);
+  } else {
+    const int threads = bj <= 128 ? 128 : 256;
+    sample_update_idx_kernel<TS><<<n2, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(bj, n2, Oh, ldo, Zb,
+                                                                                               ldz, idx, B1, ldb);
+  }
   ++*c.launches;
   return cudaGetLastError();
 }
