@@ -223,8 +223,18 @@ __global__ void __launch_bounds__(kThreads) panel_kernel(PanelArgs<TS> a) {
 //     and its wait, off the critical path.
 //   * tau = (beta - alpha) / beta and 1 / y1 come from one FP64 division,
 //     1 / (beta y1); tau = 2 exactly when the column is zero below row j.
-// The squared norm, beta, tau, 1 / y1 and T are FP64; the lazy update, the
-// products and their reductions run in the storage precision, like the
+//   * FP64 instructions are slow on this part (a dependent FP64 step costs
+//     about 64 cycles, a division or square root about 650, and the pipe
+//     executes about two lanes per clock per SM), so FP64 work is kept off
+//     the all-thread code: for FP32 rows each warp carries the squared norm
+//     in float-float arithmetic (FP64 when an entry is out of its safe
+//     range) and the sums across warps and CTAs are FP64; tau, 1 / y1 and
+//     beta come from the FP64 norm with the square root and reciprocal
+//     refined from FP32 estimates (a few dependent FP64 steps rather than
+//     an FP64 square root and division); the lazy update's coefficients
+//     and the reflector entries are FP32 as stored.
+// The global squared norm, beta, tau, 1 / y1 and T are FP64; the lazy update,
+// the products and their reductions run in the storage precision, like the
 // general kernel above.
 constexpr int kFB = 64;
 constexpr int kMaxG4 = 40;  // partial records per thread in the sums: G <= 160
@@ -269,19 +279,41 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N]) {
 // four threads per entry, fixed order.
 __device__ __forceinline__ void t_column(int jc, double tau, double* sT, const double* tv) {
   const int i = threadIdx.x >> 2, sub = threadIdx.x & 3;
-  double acc = 0.0;
-  if (i < jc)
-    for (int q = i + sub; q < jc; q += 4) acc = fma(sT[(size_t)q * kFB + i], tv[q], acc);
+  // only the needed products, in two independent chains (a dependent FP64
+  // step costs about 64 cycles here, and the FP64 pipe is narrow)
+  double a0 = 0.0, a1 = 0.0;
+  if (i < jc) {
+    int q = i + sub;
+    for (; q + 4 < jc; q += 8) {
+      a0 = fma(sT[(size_t)q * kFB + i], tv[q], a0);
+      a1 = fma(sT[(size_t)(q + 4) * kFB + i], tv[q + 4], a1);
+    }
+    if (q < jc) a0 = fma(sT[(size_t)q * kFB + i], tv[q], a0);
+  }
+  double acc = a0 + a1;
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   if (sub == 0 && i < jc) sT[(size_t)jc * kFB + i] = -tau * acc;
   if (threadIdx.x == 0) sT[(size_t)jc * kFB + jc] = tau;
 }
 
+// Float-float addition (Knuth's TwoSum for the high parts, the low parts
+// added with the rounding error): sums of squares of FP32 values carried to
+// about 2^-44 relative without FP64 arithmetic.  Commutative, so a butterfly
+// leaves the same bits in every lane.
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float err = (h - (s - bb)) + (bh - bb);
+  l = (l + bl) + err;
+  h = s;
+}
+
 template <typename TS, int TPR>
 __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a) {
   constexpr int CPT = kFB / TPR;  // columns per thread
   constexpr int LPG = 32 / TPR;   // lanes (rows) per group of a warp
+  constexpr bool kF32 = sizeof(TS) == sizeof(float);
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int bj = a.bj;
@@ -291,16 +323,18 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
   const int g = cta * a.rpc + r;
   const bool live = r < a.rpc && g < a.mt;
   const int cbase = half * CPT;
-  __shared__ TS s_tw[kFB];
-  __shared__ double s_sum[kFB];
-  __shared__ double s_row[kFB];
+  __shared__ TS s_tw[kFB];     // tau_j w_c, the lazy update's coefficients
+  __shared__ TS s_sumT[kFB];   // global dot sums of this column
+  __shared__ TS s_rowT[kFB];   // row j
+  __shared__ TS s_invT[kFB];   // 1 / y1 per finished column, storage precision
   __shared__ double s_inv[kFB];
   __shared__ double s_beta[kFB];
   __shared__ double s_tv[kFB];
   __shared__ double s_T[kFB * kFB];
   __shared__ TS s_red[kWarps][kFB];
   __shared__ double s_redx[kWarps];
-  __shared__ double s_sc[4];
+  __shared__ double s_sc[4];  // tau, 1 / y1, -, tau of the column T is completing
+  __shared__ TS s_scT[2];     // tau, 1 / y1 in the storage precision
 
   TS row[CPT];
 #pragma unroll
@@ -335,20 +369,48 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
       for (int q = 0; q < CPT; ++q)
         if (cbase + q < bj) rowb[cbase + q] = row[q];
     }
-    // (2) this row's share of the sums over rows g > j, reduced over the CTA
+    // (2) this row's share of the sums over rows g > j, reduced over the CTA;
+    // the squared norm in FP64 (float-float for FP32 rows)
     const bool below = live && g > j;
+    const bool mine = below && half == j / CPT;
     TS prod[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int c = cbase + q;
       prod[q] = (below && c != j && c < bj) ? row[q] * aj : TS(0);
     }
-    double x2 = (below && half == j / CPT) ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
+    double x2d = 0.0;
+    if constexpr (kF32) {
+      // float-float squares while every |a_j(g)| of the warp lies in
+      // [2^-60, 2^55] (no overflow or precision loss for up to 2^17 rows);
+      // otherwise this warp sums in FP64
+      const float fa = fabsf(aj);
+      const bool out_of_range = mine && aj != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
+      if (__any_sync(0xffffffffu, out_of_range)) {
+        x2d = mine ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
+        x2d = warp_sum(x2d);
+      } else {
+        float x2h = 0.f, x2l = 0.f;
+        if (mine) {
+          x2h = aj * aj;
+          x2l = fmaf(aj, aj, -x2h);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float bh = __shfl_xor_sync(0xffffffffu, x2h, o);
+          const float bl = __shfl_xor_sync(0xffffffffu, x2l, o);
+          ff_add(x2h, x2l, bh, bl);
+        }
+        if (lane == 0) x2d = static_cast<double>(x2h) + static_cast<double>(x2l);
+      }
+    } else {
+      x2d = mine ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
+      x2d = warp_sum(x2d);
+    }
     reduce_scatter<TS, CPT, LPG>(prod);
-    x2 = warp_sum(x2);
     s_red[warp][cbase + 2 * lp] = prod[0];
     s_red[warp][cbase + 2 * lp + 1] = prod[1];
-    if (lane == 0) s_redx[warp] = x2;
+    if (lane == 0) s_redx[warp] = x2d;
     __syncthreads();
     if (tid < bj) {
       TS acc = TS(0);
@@ -356,10 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
       for (int w = 0; w < kWarps; ++w) acc += s_red[w][tid];
       part[(size_t)cta * bj + tid] = acc;
     } else if (tid == kFB) {
-      double acc = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) acc += s_redx[w];
-      x2p[cta] = acc;
+      x2p[cta] = ((s_redx[0] + s_redx[1]) + (s_redx[2] + s_redx[3])) + ((s_redx[4] + s_redx[5]) + (s_redx[6] + s_redx[7]));
     }
     // (3) grid barrier; CTA 0 completes T's previous column meanwhile
     grid_arrive(a.bar);
@@ -367,14 +426,23 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
     if (!grid_wait(a.bar, G, a.err, static_cast<unsigned int>(j))) return;
     // (4) global sums in a fixed order (identical on every CTA), four threads
     // per value, every load in flight at once; CTA 0 also needs the columns < j
-    // for T.  The thread that completes the squared norm goes straight on to
-    // reflector j's FP64 scalars while the other sums finish.
+    // for T.  The squared norm (FP64) is summed by group j alone, which then
+    // goes straight on to reflector j's FP64 scalars.
     {
       const int v = tid >> 2, sub = tid & 3;
       const bool want = v < bj && (v >= j || cta == 0);
-      double acc = 0.0;
-      double alpha = 0.0;
-      if (want && v == j) {
+      TS t = TS(0);
+      double d = 0.0, alpha = 0.0;
+      if (want && v != j) {
+        TS x[kMaxG4];
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) {
+          const int q = sub + 4 * u;
+          x[u] = q < G ? __ldcg(part + (size_t)q * bj + v) : TS(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxG4; ++u) t += x[u];
+      } else if (want) {
         alpha = static_cast<double>(__ldcg(rowb + j));
         double x[kMaxG4];
 #pragma unroll
@@ -382,30 +450,47 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
           const int q = sub + 4 * u;
           x[u] = q < G ? __ldcg(x2p + q) : 0.0;
         }
+        // pairwise tree over the 40 slots (fixed shape: deterministic)
 #pragma unroll
-        for (int u = 0; u < kMaxG4; ++u) acc += x[u];
-      } else if (want) {
-        TS x[kMaxG4];
+        for (int u = 0; u < 8; ++u) x[u] += x[u + 32];
 #pragma unroll
-        for (int u = 0; u < kMaxG4; ++u) {
-          const int q = sub + 4 * u;
-          x[u] = q < G ? __ldcg(part + (size_t)q * bj + v) : TS(0);
-        }
-        TS t = TS(0);
+        for (int w = 16; w >= 1; w >>= 1)
 #pragma unroll
-        for (int u = 0; u < kMaxG4; ++u) t += x[u];
-        acc = static_cast<double>(t);
+          for (int u = 0; u < w; ++u) x[u] += x[u + w];
+        d = x[0];
       }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (sub == 0 && v < bj) s_sum[v] = acc;
+      t += __shfl_xor_sync(0xffffffffu, t, 1);
+      t += __shfl_xor_sync(0xffffffffu, t, 2);
+      if (warp == (j >> 3)) {  // the warp holding group j
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+      }
+      if (sub == 0 && want && v != j) s_sumT[v] = t;
       if (sub == 0 && v == j) {
         // (5) reflector j (FP64): beta = -sign(alpha) ||a||, y1 = alpha - beta,
         // 1 / y1 and tau = (beta - alpha) / beta from one division
-        const double x2s = acc;
+        const double x2s = d;
         const double nrm2 = fma(alpha, alpha, x2s);
         double tau = 0.0, beta = 0.0, inv = 0.0;
-        if (nrm2 > 0.0) {
+        // biased exponent of nrm2: the short-latency form when 2^-100 <= nrm2 < 2^100
+        const int ex = static_cast<int>((__double_as_longlong(nrm2) >> 52) & 0x7ff);
+        if (kF32 && ex >= 1023 - 100 && ex < 1023 + 100) {
+          // FP64 square root and reciprocal by one Newton-Raphson step from the
+          // FP32 hardware results (Markstein's method): each step doubles the
+          // correct bits, 24 -> about 47, in three dependent FP64 operations
+          // instead of an FP64 square root and division (about 650 cycles each
+          // on this part); the results are then rounded to the FP32 storage.
+          const float s0f = sqrtf(static_cast<float>(nrm2));
+          const double s0 = s0f;
+          const double nrm = fma(fma(-s0, s0, nrm2), static_cast<double>(0.5f / s0f), s0);
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          const double y1 = alpha - beta;
+          const double den = beta * y1;
+          const double r0 = static_cast<double>(1.0f / static_cast<float>(den));
+          const double rr = fma(r0, fma(-den, r0, 1.0), r0);
+          inv = beta * rr;
+          tau = x2s == 0.0 ? 2.0 : -y1 * (y1 * rr);
+        } else if (nrm2 > 0.0) {
           const double nrm = sqrt(nrm2);
           beta = alpha >= 0.0 ? -nrm : nrm;
           const double y1 = alpha - beta;
@@ -415,18 +500,26 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
         }
         s_sc[0] = tau;
         s_sc[1] = inv;
+        s_scT[0] = static_cast<TS>(tau);
+        s_scT[1] = static_cast<TS>(inv);
         s_inv[j] = inv;
+        s_invT[j] = static_cast<TS>(inv);
         s_beta[j] = beta;
         if (cta == 0) a.tau[j] = static_cast<TS>(tau);
       }
     }
-    if (tid < bj) s_row[tid] = static_cast<double>(__ldcg(rowb + tid));
+    if (tid < bj) s_rowT[tid] = __ldcg(rowb + tid);
     __syncthreads();
-    const double tau = s_sc[0], inv = s_sc[1];
-    if (tid > j && tid < bj) s_tw[tid] = static_cast<TS>(tau * fma(s_sum[tid], inv, s_row[tid]));
-    if (cta == 0 && tid < j) s_tv[tid] = s_inv[tid] * fma(s_sum[tid], inv, s_row[tid]);
-    if (cta == 0 && tid == 0) s_sc[3] = tau;
-    vprev = !live ? TS(0) : (g > j ? static_cast<TS>(static_cast<double>(aj) * inv) : (g == j ? TS(1) : TS(0)));
+    // (6) the lazy update's coefficients and this row's entry of reflector j,
+    // in the storage precision; CTA 0 also forms (Y^T v_j) for T in FP64
+    {
+      const TS tauT = s_scT[0], invT = s_scT[1];
+      if (tid > j && tid < bj) s_tw[tid] = tauT * fma(s_sumT[tid], invT, s_rowT[tid]);
+      vprev = !live ? TS(0) : (g > j ? aj * invT : (g == j ? TS(1) : TS(0)));
+    }
+    if (cta == 0 && tid < j)
+      s_tv[tid] = s_inv[tid] * fma(static_cast<double>(s_sumT[tid]), s_sc[1], static_cast<double>(s_rowT[tid]));
+    if (cta == 0 && tid == 0) s_sc[3] = s_sc[0];
     __syncthreads();
   }
   grid_exit(a.bar, G);
@@ -441,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
       if (c >= bj) continue;
       TS op, oy;
       if (g > c) {
-        op = static_cast<TS>(static_cast<double>(row[q]) * s_inv[c]);
+        op = row[q] * s_invT[c];
         oy = op;
       } else if (g == c) {
         op = static_cast<TS>(s_beta[c]);

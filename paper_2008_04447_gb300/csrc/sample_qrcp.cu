@@ -10,8 +10,9 @@
 //      column values) to a double-buffered candidate table;
 //   2. one grid barrier;
 //   3. every CTA reduces the table in the same order (so all agree bit for
-//      bit), rebuilds the Householder vector of the winner in FP64 (tau from
-//      the vector as stored), applies it to its alive columns in the storage
+//      bit), rebuilds the Householder vector of the winner in FP64 (tau =
+//      (beta - alpha) / beta, with 1 / y1 from the same division), applies
+//      it (rounded to the storage precision) to its alive columns in the storage
 //      precision and downdates their FP64 squared norms (removing the
 //      contribution of the finished row, Alg. 1), recomputing a norm from
 //      the remaining rows when the downdated value has fallen to sqrt(eps)
@@ -33,6 +34,27 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSteps = 256;
 constexpr int kMaxRecS = 8;  // candidate records per lane: G <= 256
+
+// The squared norms compared here are never negative, and for non-negative
+// doubles the IEEE order is the order of their bit patterns as integers, so
+// the argmax compares 64-bit integers (an FP64 comparison is a long-latency
+// operation on this part).  Ties go to the lowest current position; p < 0 =
+// empty.
+__device__ __forceinline__ bool better_key(long long k1, int p1, long long k2, int p2) {
+  if (p2 < 0) return p1 >= 0;
+  if (p1 < 0) return false;
+  return (k1 > k2) || (k1 == k2 && p1 < p2);
+}
+
+__device__ __forceinline__ void warp_argmax_key(long long& k, int& p, int& tag) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+    const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+    const int t2 = __shfl_xor_sync(0xffffffffu, tag, o);
+    if (better_key(k2, p2, k, p)) { k = k2; p = p2; tag = t2; }
+  }
+}
 
 template <typename TS>
 struct SqArgs {
@@ -68,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
   TS* vv = s + (size_t)l * cpc;               // l
   int* pos = reinterpret_cast<int*>(vv + l + 1);
   int* alive = pos + cpc;
-  __shared__ double red_v[kWarps];
+  __shared__ long long red_v[kWarps];
   __shared__ int red_p[kWarps], red_t[kWarps];
   __shared__ int s_best_lc, s_win_cta, s_win_pos;
   __shared__ double s_tau;
@@ -98,21 +120,23 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     const int par = i & 1;
     double* tab = a.cand + (size_t)par * G * rec;
     // (1) local best alive column
-    double bv = -1.0;
+    long long bv = 0;
     int bp = -1, bt = -1;
-    for (int c = tid; c < nc; c += kThreads)
-      if (alive[c] && better(nu2[c], pos[c], bv, bp)) { bv = nu2[c]; bp = pos[c]; bt = c; }
-    warp_argmax(bv, bp, bt);
+    for (int c = tid; c < nc; c += kThreads) {
+      const long long kc = __double_as_longlong(nu2[c]);
+      if (alive[c] && better_key(kc, pos[c], bv, bp)) { bv = kc; bp = pos[c]; bt = c; }
+    }
+    warp_argmax_key(bv, bp, bt);
     if (lane == 0) { red_v[warp] = bv; red_p[warp] = bp; red_t[warp] = bt; }
     __syncthreads();
     if (warp == 0) {
-      bv = lane < kWarps ? red_v[lane] : -1.0;
+      bv = lane < kWarps ? red_v[lane] : 0;
       bp = lane < kWarps ? red_p[lane] : -1;
       bt = lane < kWarps ? red_t[lane] : -1;
-      warp_argmax(bv, bp, bt);
+      warp_argmax_key(bv, bp, bt);
       if (lane == 0) {
         s_best_lc = bt;
-        tab[(size_t)cta * rec + 0] = bv;
+        tab[(size_t)cta * rec + 0] = __longlong_as_double(bv);
         tab[(size_t)cta * rec + 1] = static_cast<double>(bp);
       }
     }
@@ -126,22 +150,22 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
     if (!grid_barrier(a.bar, G, a.err, epoch)) return;
     // (3) global winner: same reduction order on every CTA
     if (warp == 0) {
-      double gv = -1.0;
+      long long gv = 0;
       int gp = -1, gt = -1;
-      double vs[kMaxRecS], ps[kMaxRecS];
+      long long vs[kMaxRecS];
+      int ps[kMaxRecS];
 #pragma unroll
       for (int u = 0; u < kMaxRecS; ++u) {
         const int q = lane + 32 * u;
-        vs[u] = q < G ? __ldcg(tab + (size_t)q * rec + 0) : -1.0;
-        ps[u] = q < G ? __ldcg(tab + (size_t)q * rec + 1) : -1.0;
+        vs[u] = q < G ? __double_as_longlong(__ldcg(tab + (size_t)q * rec + 0)) : 0;
+        ps[u] = q < G ? static_cast<int>(__ldcg(tab + (size_t)q * rec + 1)) : -1;
       }
 #pragma unroll
       for (int u = 0; u < kMaxRecS; ++u) {
         const int q = lane + 32 * u;
-        const int p = static_cast<int>(ps[u]);
-        if (q < G && better(vs[u], p, gv, gp)) { gv = vs[u]; gp = p; gt = q; }
+        if (q < G && better_key(vs[u], ps[u], gv, gp)) { gv = vs[u]; gp = ps[u]; gt = q; }
       }
-      warp_argmax(gv, gp, gt);
+      warp_argmax_key(gv, gp, gt);
       if (lane == 0) { s_win_cta = gt; s_win_pos = gp; }
     }
     __syncthreads();
@@ -162,29 +186,30 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
       x2 = warp_sum(x2);
       const double alpha = wcol[i];
       const double nrm2 = fma(alpha, alpha, x2);
-      double beta = 0.0, inv = 0.0;
+      double beta = 0.0, inv = 0.0, tau = 0.0;
       const bool zero = !(nrm2 > 0.0);
       if (!zero) {
+        // one division: 1 / y1 = beta / (beta y1), tau = (beta - alpha) / beta = -y1 / beta
         const double nrm = sqrt(nrm2);
         beta = alpha >= 0.0 ? -nrm : nrm;
-        inv = 1.0 / (alpha - beta);
+        const double y1 = alpha - beta;
+        const double rr = 1.0 / (beta * y1);
+        inv = beta * rr;
+        tau = x2 == 0.0 ? 2.0 : -y1 * (y1 * rr);
       }
       if (cta == 0) {
         double* col = a.S11 + (size_t)i * a.lds;
         for (int r = lane; r < steps; r += 32) col[r] = r < i ? wcol[r] : (r == i ? beta : 0.0);
       }
       __syncwarp();
-      double v2 = 0.0;
       for (int r = lane; r < l; r += 32) {
         TS v;
         if (r < i) v = TS(0);
         else if (r == i) v = TS(1);
         else v = static_cast<TS>(wcol[r] * inv);
         vv[r] = v;
-        if (r > i) v2 = fma(static_cast<double>(v), static_cast<double>(v), v2);
       }
-      v2 = warp_sum(v2);
-      if (lane == 0) s_tau = zero ? 0.0 : 2.0 / (1.0 + v2);
+      if (lane == 0) s_tau = tau;
     }
     __syncthreads();
     const TS tau = static_cast<TS>(s_tau);
