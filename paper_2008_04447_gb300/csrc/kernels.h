@@ -42,6 +42,10 @@ cudaError_t tc_gemm_tn(const Ctx& c, int M, int N, int K, float alpha, const flo
 // Same with A M-major (M x K column-major): C = alpha A B + beta C.
 cudaError_t tc_gemm_nn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
                        int ldb, float beta, float* C, int ldc, bool split3);
+// C = A B (A M x K, M-major; B K x N, K-major) with both inputs rounded to
+// bfloat16 and FP32 accumulation on the tensor cores (K chunks of at most 1024).
+cudaError_t tc_gemm_nn_bf16(const Ctx& c, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                            float* C, int ldc);
 
 // Partial QRCP of the sample (l x nt): `steps` pivots, norms downdated.
 // Writes S11 (steps x steps, FP64, ld lds), swaps[steps], src[nt] (old position

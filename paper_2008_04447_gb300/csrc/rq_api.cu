@@ -356,7 +356,10 @@ template <typename TS>
 cudaError_t sketch_gemm(const Ctx& c, bool mixed, int l, int n, int m, const TS* Omega, int ldo, const TS* A, int lda,
                         TS* B) {
   if constexpr (sizeof(TS) == sizeof(float)) {
-    if (mixed) return gemm_bf16_inputs(c, l, n, m, Omega, ldo, A, lda, B, l);
+    if (mixed) {
+      if (tc_gemm_supported(Omega, ldo, A, lda)) return tc_gemm_nn_bf16(c, l, n, m, Omega, ldo, A, lda, B, l);
+      return gemm_bf16_inputs(c, l, n, m, Omega, ldo, A, lda, B, l);
+    }
   }
   return prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), B, l);
 }

@@ -22,9 +22,14 @@
 // the Ahi*Bhi products go to one TMEM accumulator and the two correction
 // products (2^-11 smaller) to a second one, and long K is cut into chunks of
 // at most 1024 whose partial results are added in IEEE FP32 (split-K reduce).
+// With bf16 set, both slices are instead rounded to bfloat16 in place (round
+// to nearest even) and one plain TF32 MMA per K=8 step follows: bfloat16
+// values are exact in TF32 and their products exact in FP32, so this is the
+// BF16-input, FP32-accumulate product of the reduced-precision sketch.
 // All waits are bounded; on a timeout the kernel records RQ_ETIMEOUT, lets
 // its copies land, frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 #include "common.cuh"
@@ -111,6 +116,16 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ float4 bf16r4(float4 x) {
+  x.x = bf16r(x.x);
+  x.y = bf16r(x.y);
+  x.z = bf16r(x.z);
+  x.w = bf16r(x.w);
+  return x;
+}
+
 struct TcArgs {
   int M, N, K;       // full problem
   int kchunk;        // K range of blockIdx.z
@@ -120,6 +135,7 @@ struct TcArgs {
   int transC;        // store C^T (C is N x M)
   size_t czs;        // blockIdx.z stride of C (split-K partials)
   int split3;        // 3xTF32 (1) or plain TF32 (0)
+  int bf16;          // round both operands to bfloat16 first (plain TF32 MMA)
   int* err;
 };
 
@@ -246,8 +262,8 @@ __global__ void __launch_bounds__(kTcThreads)
             h.x = tf32_hi(x.x); h.y = tf32_hi(x.y); h.z = tf32_hi(x.z); h.w = tf32_hi(x.w);
             l.x = tf32_hi(x.x - h.x); l.y = tf32_hi(x.y - h.y); l.z = tf32_hi(x.z - h.z); l.w = tf32_hi(x.w - h.w);
           } else {
-            h = x;
-            l = x;
+            h = a.bf16 ? bf16r4(x) : x;
+            l = h;
           }
           ah[q ^ (t & 7)] = h;
           if (a.split3) al[q ^ (t & 7)] = l;
@@ -274,6 +290,13 @@ __global__ void __launch_bounds__(kTcThreads)
           bh[e] = h;
           bl[e] = l;
         }
+      } else if (a.bf16) {
+        if (!AMN) {
+          float4* ah = reinterpret_cast<float4*>(a_hi(s));
+          for (int e = t; e < (int)(ABYTES / 16); e += 128) ah[e] = bf16r4(ah[e]);
+        }
+        float4* bh = reinterpret_cast<float4*>(b_hi(s));
+        for (int e = t; e < (int)(BBYTES / 16); e += 128) bh[e] = bf16r4(bh[e]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(ready(s));
@@ -425,7 +448,8 @@ bool tc_gemm_supported(const float* A, int lda, const float* B, int ldb) {
 
 namespace {
 cudaError_t tc_gemm_any(const Ctx& c, bool amn, int M, int N, int K, float alpha, const float* A, int lda,
-                        const float* B, int ldb, float beta, float* C, int ldc, bool transC, bool split3) {
+                        const float* B, int ldb, float beta, float* C, int ldc, bool transC, bool split3,
+                        bool bf16 = false) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (!tc_gemm_supported(A, lda, B, ldb)) return cudaErrorNotSupported;
   // 64-column tiles when N is small or K is short (two CTAs per SM, so one
@@ -437,10 +461,11 @@ cudaError_t tc_gemm_any(const Ctx& c, bool amn, int M, int N, int K, float alpha
   const int tiles = ((M + TBM - 1) / TBM) * ((N + bn - 1) / bn);
   int S = 1;
   if (c.splitk && K > 1024) {
-    // enough CTAs to fill the GPU, and (3xTF32) no chunk longer than 1024
+    // enough CTAs to fill the GPU, and (3xTF32, BF16 inputs) no chunk longer
+    // than 1024: the tensor core's accumulation bias grows with the chunk
     S = tiles < 2 * c.num_sms ? (2 * c.num_sms + tiles - 1) / tiles : 1;
     if (S > K / 512) S = K / 512;
-    if (split3 && S < (K + 1023) / 1024) S = (K + 1023) / 1024;
+    if ((split3 || bf16) && S < (K + 1023) / 1024) S = (K + 1023) / 1024;
     const size_t cap = c.splitk_bytes / (sizeof(float) * (size_t)M * N);
     if ((size_t)S > cap) S = (int)cap;
     if (S < 2) S = 1;
@@ -455,7 +480,8 @@ cudaError_t tc_gemm_any(const Ctx& c, bool amn, int M, int N, int K, float alpha
   args.N = N;
   args.K = K;
   args.kchunk = kchunk;
-  args.split3 = split3 ? 1 : 0;
+  args.split3 = split3 && !bf16 ? 1 : 0;
+  args.bf16 = bf16 ? 1 : 0;
   args.err = c.err;
   if (S == 1) {
     args.alpha = alpha;
@@ -490,6 +516,11 @@ cudaError_t tc_gemm_tn(const Ctx& c, int M, int N, int K, float alpha, const flo
 cudaError_t tc_gemm_nn(const Ctx& c, int M, int N, int K, float alpha, const float* A, int lda, const float* B,
                        int ldb, float beta, float* C, int ldc, bool split3) {
   return tc_gemm_any(c, true, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, false, split3);
+}
+
+cudaError_t tc_gemm_nn_bf16(const Ctx& c, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                            float* C, int ldc) {
+  return tc_gemm_any(c, true, M, N, K, 1.f, A, lda, B, ldb, 0.f, C, ldc, false, false, true);
 }
 
 }  // namespace rq
