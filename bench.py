@@ -130,6 +130,13 @@ def run_sweep(args):
             torch.cuda.empty_cache()
 
 
+# DRAM bytes moved per factorisation by the trailing-update kernels (the W^T
+# GEMM, the A2 update GEMM and the split-K reduce) of the FP64 16384 x 16384
+# workload, from the ncu capture summarised in
+# profiles/rqrcp_fp64_16384_launches.md (valid while those kernels are unchanged).
+TRAILING_DRAM_BYTES_FP64_16384 = 556.3e9
+
+
 def flops_qr(m, n):
     """Householder QR flops: 4mnk - 2(m+n)k^2 + 4k^3/3, k = min(m, n) (= 4/3 n^3 for m = n)."""
     k = min(m, n)
@@ -510,8 +517,12 @@ def main():
                   "gbs": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None, "launches": v[3] // args.steps}
               for k, v in prof.items()}
     achieved = tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None
+    measured = args.prec == "fp64" and n == 16384 and b == 64
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": TRAILING_DRAM_BYTES_FP64_16384 if measured else None,
+                "traffic_scope": "DRAM bytes per step of all trailing-update launches (ncu)",
+                "algorithmic_bytes": tr[2] / args.steps,
                 "kernel": "trailing update (block reflector GEMMs), FP64",
                 "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop (FP64 pipe, nominal)"}
 
