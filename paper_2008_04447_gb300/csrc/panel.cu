@@ -469,35 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
       if (sub == 0 && v == j) {
         // (5) reflector j (FP64): beta = -sign(alpha) ||a||, y1 = alpha - beta,
         // 1 / y1 and tau = (beta - alpha) / beta from one division
-        const double x2s = d;
-        const double nrm2 = fma(alpha, alpha, x2s);
-        double tau = 0.0, beta = 0.0, inv = 0.0;
-        // biased exponent of nrm2: the short-latency form when 2^-100 <= nrm2 < 2^100
-        const int ex = static_cast<int>((__double_as_longlong(nrm2) >> 52) & 0x7ff);
-        if (kF32 && ex >= 1023 - 100 && ex < 1023 + 100) {
-          // FP64 square root and reciprocal by one Newton-Raphson step from the
-          // FP32 hardware results (Markstein's method): each step doubles the
-          // correct bits, 24 -> about 47, in three dependent FP64 operations
-          // instead of an FP64 square root and division (about 650 cycles each
-          // on this part); the results are then rounded to the FP32 storage.
-          const float s0f = sqrtf(static_cast<float>(nrm2));
-          const double s0 = s0f;
-          const double nrm = fma(fma(-s0, s0, nrm2), static_cast<double>(0.5f / s0f), s0);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          const double y1 = alpha - beta;
-          const double den = beta * y1;
-          const double r0 = static_cast<double>(1.0f / static_cast<float>(den));
-          const double rr = fma(r0, fma(-den, r0, 1.0), r0);
-          inv = beta * rr;
-          tau = x2s == 0.0 ? 2.0 : -y1 * (y1 * rr);
-        } else if (nrm2 > 0.0) {
-          const double nrm = sqrt(nrm2);
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          const double y1 = alpha - beta;
-          const double rr = 1.0 / (beta * y1);
-          inv = beta * rr;
-          tau = x2s == 0.0 ? 2.0 : -y1 * (y1 * rr);
-        }
+        double tau, beta, inv;
+        householder_scalars(alpha, d, kF32, beta, inv, tau);
         s_sc[0] = tau;
         s_sc[1] = inv;
         s_scT[0] = static_cast<TS>(tau);

@@ -185,18 +185,8 @@ __global__ void __launch_bounds__(kThreads) sample_qrcp_kernel(SqArgs<TS> a) {
       for (int r = i + 1 + lane; r < l; r += 32) x2 = fma(wcol[r], wcol[r], x2);
       x2 = warp_sum(x2);
       const double alpha = wcol[i];
-      const double nrm2 = fma(alpha, alpha, x2);
-      double beta = 0.0, inv = 0.0, tau = 0.0;
-      const bool zero = !(nrm2 > 0.0);
-      if (!zero) {
-        // one division: 1 / y1 = beta / (beta y1), tau = (beta - alpha) / beta = -y1 / beta
-        const double nrm = sqrt(nrm2);
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        const double y1 = alpha - beta;
-        const double rr = 1.0 / (beta * y1);
-        inv = beta * rr;
-        tau = x2 == 0.0 ? 2.0 : -y1 * (y1 * rr);
-      }
+      double beta, inv, tau;
+      householder_scalars(alpha, x2, sizeof(TS) == sizeof(float), beta, inv, tau);
       if (cta == 0) {
         double* col = a.S11 + (size_t)i * a.lds;
         for (int r = lane; r < steps; r += 32) col[r] = r < i ? wcol[r] : (r == i ? beta : 0.0);
