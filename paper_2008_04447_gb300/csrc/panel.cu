@@ -354,11 +354,18 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
     // (1) reflector j-1 on this row's columns >= j; pick up a_j(g)
     TS aj = TS(0);
     const bool upd = j > 0 && live && g >= j - 1;
+    // finished columns (c < j) never change again: chunks of 16 columns that
+    // lie wholly below j are skipped
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      const int c = cbase + q;
-      if (upd && c >= j && c < bj) row[q] = fma(-s_tw[c], vprev, row[q]);
-      if (c == j) aj = row[q];
+    for (int q0 = 0; q0 < CPT; q0 += 16) {
+      if (cbase + q0 + 16 > j) {
+#pragma unroll
+        for (int q = q0; q < q0 + 16; ++q) {
+          const int c = cbase + q;
+          if (upd && c >= j && c < bj) row[q] = fma(-s_tw[c], vprev, row[q]);
+          if (c == j) aj = row[q];
+        }
+      }
     }
     if (TPR == 2) {
       const TS o = __shfl_xor_sync(0xffffffffu, aj, 16);
@@ -373,6 +380,8 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
     // the squared norm in FP64 (float-float for FP32 rows)
     const bool below = live && g > j;
     const bool mine = below && half == j / CPT;
+    // (the products with finished columns, c < j, feed T's sums, which need
+    // every CTA's rows)
     TS prod[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
