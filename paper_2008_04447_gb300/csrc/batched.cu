@@ -31,17 +31,6 @@ constexpr int kMaxLB = 128;  // largest sample rank of the batched path
 constexpr int kStageFloats = 50 * 1024;  // 200 KB
 constexpr int kMaxDevices = 64;
 
-__device__ __forceinline__ double bsum_d(double v, double* red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) t += red[w];
-  return t;
-}
-
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // C (M x N) = alpha op(A) op(B) + beta C, FP32, block-level (all NT threads).
@@ -162,9 +151,11 @@ __device__ void gemm_b(int M, int N, int K, float alpha, const float* A, int lda
 
 struct Shm {
   double redd[NW];
+  long long redk[NW];
   float redf[NW];
-  double vv[kMaxLB];
   double sc[4];
+  float scf[4];
+  float vf[kMaxLB];
   int si[4];
   int wp[NW];
   float dots[NW][kMaxBB];
@@ -181,27 +172,51 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
   for (int e = tid; e < bj * bj; e += NT) T[(e % bj) + (size_t)(e / bj) * ldt] = 0.0;
   for (int j = 0; j < bj; ++j) {
     float* aj = P + (size_t)j * ldp;
-    double x2 = 0.0;
-    for (int g = j + 1 + tid; g < mt; g += NT) x2 = fma((double)aj[g], (double)aj[g], x2);
-    x2 = bsum_d(x2, s.redd);
-    if (tid == 0) {
-      const double alpha = aj[j];
-      const double nrm2 = fma(alpha, alpha, x2);
-      double tu = 0.0, beta = 0.0, y1 = 1.0;
-      if (nrm2 > 0.0) {
-        const double nrm = sqrt(nrm2);
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        y1 = alpha - beta;
-        tu = 2.0 / (1.0 + x2 / (y1 * y1));
+    // squared norm below row j with FP64 accuracy: float-float per thread and
+    // warp (FP64 for a warp holding an entry outside [2^-60, 2^55]), combined
+    // in FP64 by thread 0, which forms the reflector's scalars (FP64 is slow
+    // on this part, so it stays off the all-thread path)
+    {
+      float xh = 0.f, xl = 0.f;
+      bool oor = false;
+      for (int g = j + 1 + tid; g < mt; g += NT) {
+        const float a = aj[g], fa = fabsf(a);
+        oor |= a != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
+        const float pp = a * a;
+        ff_add(xh, xl, pp, fmaf(a, a, -pp));
       }
+      double xd = 0.0;
+      if (__any_sync(0xffffffffu, oor)) {
+        for (int g = j + 1 + tid; g < mt; g += NT) xd = fma((double)aj[g], (double)aj[g], xd);
+        xd = warp_sum(xd);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float bh = __shfl_xor_sync(0xffffffffu, xh, o);
+          const float bl = __shfl_xor_sync(0xffffffffu, xl, o);
+          ff_add(xh, xl, bh, bl);
+        }
+        if (lane == 0) xd = (double)xh + (double)xl;
+      }
+      if (lane == 0) s.redd[warp] = xd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double x2 = ((s.redd[0] + s.redd[1]) + (s.redd[2] + s.redd[3])) + ((s.redd[4] + s.redd[5]) + (s.redd[6] + s.redd[7]));
+      double beta, inv, tu;
+      householder_scalars((double)aj[j], x2, true, beta, inv, tu);
       s.sc[0] = tu;
-      s.sc[1] = y1;
       s.sc[2] = beta;
+      s.scf[0] = (float)tu;
+      s.scf[1] = (float)inv;
       tau[j] = (float)tu;
     }
     __syncthreads();
-    const double tu = s.sc[0], y1 = s.sc[1];
-    for (int g = j + 1 + tid; g < mt; g += NT) aj[g] = tu != 0.0 ? (float)((double)aj[g] / y1) : 0.f;
+    const double tu = s.sc[0];
+    {
+      const float invf = s.scf[1];
+      for (int g = j + 1 + tid; g < mt; g += NT) aj[g] *= invf;
+    }
     __syncthreads();
     // d_c = sum_{g > j} v_g P(g, c) for every other column c of the panel,
     // sixteen columns at a time
@@ -231,7 +246,7 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
     }
     __syncthreads();
     // w_c = P(j, c) + d_c for c > j; (Y^T v)_i = y_i(j) + d_i for i < j
-    if (tid > j && tid < bj) s.tw[tid] = (float)(tu * ((double)P[j + (size_t)tid * ldp] + (double)s.dots[0][tid]));
+    if (tid > j && tid < bj) s.tw[tid] = s.scf[0] * (P[j + (size_t)tid * ldp] + s.dots[0][tid]);
     if (tid < j) s.tvec[tid] = (double)P[j + (size_t)tid * ldp] + (double)s.dots[0][tid];
     __syncthreads();
     // columns c > j: P(:, c) -= tau w_c v
@@ -240,11 +255,23 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
       float* ac = P + (size_t)c * ldp;
       for (int g = j + tid; g < mt; g += NT) ac[g] = fmaf(-tw, g == j ? 1.f : aj[g], ac[g]);
     }
-    // T(0:j, j) = -tau T(0:j, 0:j) (Y^T v)
-    if (tid < j) {
-      double acc = 0.0;
-      for (int q = tid; q < j; ++q) acc = fma(T[tid + (size_t)q * ldt], s.tvec[q], acc);
-      T[tid + (size_t)j * ldt] = -tu * acc;
+    // T(0:j, j) = -tau T(0:j, 0:j) (Y^T v): four threads per entry, two
+    // independent chains each (short FP64 dependency chains)
+    {
+      const int ti = tid >> 2, sub = tid & 3;
+      double a0 = 0.0, a1 = 0.0;
+      if (ti < j) {
+        int q = ti + sub;
+        for (; q + 4 < j; q += 8) {
+          a0 = fma(T[ti + (size_t)q * ldt], s.tvec[q], a0);
+          a1 = fma(T[ti + (size_t)(q + 4) * ldt], s.tvec[q + 4], a1);
+        }
+        if (q < j) a0 = fma(T[ti + (size_t)q * ldt], s.tvec[q], a0);
+      }
+      double acc = a0 + a1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (sub == 0 && ti < j) T[ti + (size_t)j * ldt] = -tu * acc;
     }
     if (tid == 0) {
       T[j + (size_t)j * ldt] = tu;
@@ -266,25 +293,42 @@ __device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, doubl
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double tol = 3.4526698300124393e-04;  // sqrt(FLT_EPSILON): the sample is held in FP32
   for (int c = tid; c < nt; c += NT) {
-    double acc = 0.0;
-    for (int r = 0; r < l; ++r) acc = fma((double)B[r + (size_t)c * l], (double)B[r + (size_t)c * l], acc);
+    // squared column norm with FP64 accuracy in float-float arithmetic (FP64
+    // when an entry lies outside [2^-60, 2^55])
+    const float* bc = B + (size_t)c * l;
+    float h = 0.f, lo = 0.f;
+    bool oor = false;
+    for (int r = 0; r < l; ++r) {
+      const float a = bc[r], fa = fabsf(a);
+      oor |= a != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
+      const float pp = a * a;
+      ff_add(h, lo, pp, fmaf(a, a, -pp));
+    }
+    double acc = (double)h + (double)lo;
+    if (oor) {
+      acc = 0.0;
+      for (int r = 0; r < l; ++r) acc = fma((double)bc[r], (double)bc[r], acc);
+    }
     nu2[c] = acc;
     ref2[c] = acc;
   }
   __syncthreads();
   for (int i = 0; i < steps; ++i) {
-    double bv = -1.0;
+    // argmax on the squared norms' bit patterns (non-negative doubles)
+    long long bv = 0;
     int bp = -1, dummy = 0;
-    for (int c = i + tid; c < nt; c += NT)
-      if (better(nu2[c], c, bv, bp)) { bv = nu2[c]; bp = c; }
-    warp_argmax(bv, bp, dummy);
-    if (lane == 0) { s.redd[warp] = bv; s.wp[warp] = bp; }
+    for (int c = i + tid; c < nt; c += NT) {
+      const long long kc = __double_as_longlong(nu2[c]);
+      if (better_key(kc, c, bv, bp)) { bv = kc; bp = c; }
+    }
+    warp_argmax_key(bv, bp, dummy);
+    if (lane == 0) { s.redk[warp] = bv; s.wp[warp] = bp; }
     __syncthreads();
     if (tid == 0) {
-      double gv = -1.0;
+      long long gv = 0;
       int gp = -1;
       for (int w = 0; w < NW; ++w)
-        if (better(s.redd[w], s.wp[w], gv, gp)) { gv = s.redd[w]; gp = s.wp[w]; }
+        if (better_key(s.redk[w], s.wp[w], gv, gp)) { gv = s.redk[w]; gp = s.wp[w]; }
       s.si[1] = gp;
     }
     __syncthreads();
@@ -307,35 +351,28 @@ __device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, doubl
       double x2 = 0.0;
       for (int r = i + 1 + lane; r < l; r += 32) x2 = fma((double)bi[r], (double)bi[r], x2);
       x2 = warp_sum(x2);
-      const double alpha = bi[i];
-      const double nrm2 = fma(alpha, alpha, x2);
-      double beta = 0.0, y1 = 1.0;
-      const bool zero = !(nrm2 > 0.0);
-      if (!zero) {
-        const double nrm = sqrt(nrm2);
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        y1 = alpha - beta;
-      }
+      double beta, inv, tau;
+      householder_scalars((double)bi[i], x2, true, beta, inv, tau);
       for (int r = lane; r < steps; r += 32) S11[r + (size_t)i * lds] = r < i ? (double)bi[r] : (r == i ? beta : 0.0);
-      double v2 = 0.0;
-      for (int r = lane; r < l; r += 32) {
-        const double v = r < i ? 0.0 : (r == i ? 1.0 : (zero ? 0.0 : (double)bi[r] / y1));
-        s.vv[r] = v;
-        if (r > i) v2 = fma(v, v, v2);
-      }
-      v2 = warp_sum(v2);
-      if (lane == 0) { s.sc[0] = zero ? 0.0 : 2.0 / (1.0 + v2); s.sc[2] = beta; }
+      const float invf = (float)inv;
+      for (int r = lane; r < l; r += 32) s.vf[r] = r < i ? 0.f : (r == i ? 1.f : bi[r] * invf);
+      if (lane == 0) { s.sc[0] = tau; s.sc[2] = beta; }
     }
     __syncthreads();
     const float tu = (float)s.sc[0];
     for (int c = i + 1 + tid; c < nt; c += NT) {
       float* bc = B + (size_t)c * l;
       if (tu != 0.f) {
-        float w = bc[i];
-        for (int r = i + 1; r < l; ++r) w = fmaf((float)s.vv[r], bc[r], w);
-        const float tw = tu * w;
+        float w0 = bc[i], w1 = 0.f;
+        int r = i + 1;
+        for (; r + 1 < l; r += 2) {
+          w0 = fmaf(s.vf[r], bc[r], w0);
+          w1 = fmaf(s.vf[r + 1], bc[r + 1], w1);
+        }
+        if (r < l) w0 = fmaf(s.vf[r], bc[r], w0);
+        const float tw = tu * (w0 + w1);
         bc[i] -= tw;
-        for (int r = i + 1; r < l; ++r) bc[r] = fmaf(-tw, (float)s.vv[r], bc[r]);
+        for (int r2 = i + 1; r2 < l; ++r2) bc[r2] = fmaf(-tw, s.vf[r2], bc[r2]);
       }
       const double x = bc[i];
       double nn = nu2[c] - x * x;
@@ -548,24 +585,39 @@ __device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool
     }
     __syncthreads();
     if (j0 + bj < k) {
-      // Eq. (update1): Omegahat11 = S11 R11^{-1} (FP64), B1 = S12 - Omegahat11 R12
+      // Eq. (update1): Omegahat11 = S11 R11^{-1} by forward substitution along
+      // each row in FP64 (four threads per row, the diagonal's reciprocals
+      // first: FP64 division and long FP64 chains are slow on this part), then
+      // B1 = S12 - Omegahat11 R12 accumulated in FP32 like the sample itself
       if (tid < bj) {
-        const int r = tid;
+        const double d = w.P[j0 + tid + (size_t)tid * m];
+        s.tvec[tid] = d != 0.0 ? 1.0 / d : 0.0;
+      }
+      __syncthreads();
+      {
+        const int r = tid >> 2, sub = tid & 3;
         for (int j = 0; j < bj; ++j) {
-          double acc = j >= r ? w.S11[r + (size_t)j * b] : 0.0;
-          for (int i = r; i < j; ++i) acc -= w.Oh[r + (size_t)i * b] * (double)w.P[j0 + i + (size_t)j * m];
-          const double d = w.P[j0 + j + (size_t)j * m];
-          w.Oh[r + (size_t)j * b] = (j < r || d == 0.0) ? 0.0 : acc / d;
+          double acc = 0.0;
+          if (r < bj)
+            for (int i = r + sub; i < j; i += 4)
+              acc = fma(w.Oh[r + (size_t)i * b], (double)w.P[j0 + i + (size_t)j * m], acc);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          if (r < bj && sub == 0) w.Oh[r + (size_t)j * b] = j < r ? 0.0 : (w.S11[r + (size_t)j * b] - acc) * s.tvec[j];
+          __syncwarp();
         }
       }
+      __syncthreads();
+      float* sO = sm;  // Omegahat11 rounded to FP32 (the staging area is free here)
+      for (int e = tid; e < bj * bj; e += NT) sO[e] = (float)w.Oh[(e % bj) + (size_t)(e / bj) * b];
       __syncthreads();
       float* B1 = BJ + (size_t)bj * l;
       for (int e = tid; e < bj * n2; e += NT) {
         const int r = e % bj, t = e / bj;
         const float* zc = w.Z + j0 + (size_t)w.jp[j0 + bj + t] * k;
-        double acc = 0.0;
-        for (int i = r; i < bj; ++i) acc = fma(w.Oh[r + (size_t)i * b], (double)zc[i], acc);
-        B1[r + (size_t)t * l] = (float)((double)B1[r + (size_t)t * l] - acc);
+        float acc = 0.f;
+        for (int i = r; i < bj; ++i) acc = fmaf(sO[r + i * bj], zc[i], acc);
+        B1[r + (size_t)t * l] -= acc;
       }
       __syncthreads();
     }

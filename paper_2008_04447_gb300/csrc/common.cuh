@@ -121,6 +121,39 @@ __device__ __forceinline__ void warp_argmax(double& v, int& p, int& tag) {
   }
 }
 
+// Float-float addition (Knuth's TwoSum for the high parts, the low parts
+// added with the rounding error): sums of squares of FP32 values carried to
+// about 2^-44 relative without FP64 arithmetic.  Commutative, so a butterfly
+// leaves the same bits in every lane.
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float err = (h - (s - bb)) + (bh - bb);
+  l = (l + bl) + err;
+  h = s;
+}
+
+// Pivot argmax over squared norms, which are never negative: for non-negative
+// doubles the IEEE order is the order of their bit patterns as integers, so
+// the argmax compares 64-bit integers (an FP64 comparison is a long-latency
+// operation on this part).  Ties go to the lowest current position; p < 0 =
+// empty.
+__device__ __forceinline__ bool better_key(long long k1, int p1, long long k2, int p2) {
+  if (p2 < 0) return p1 >= 0;
+  if (p1 < 0) return false;
+  return (k1 > k2) || (k1 == k2 && p1 < p2);
+}
+
+__device__ __forceinline__ void warp_argmax_key(long long& k, int& p, int& tag) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+    const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+    const int t2 = __shfl_xor_sync(0xffffffffu, tag, o);
+    if (better_key(k2, p2, k, p)) { k = k2; p = p2; tag = t2; }
+  }
+}
+
 // Householder scalars of a column with leading entry alpha and squared norm
 // x2 below it (Sec. 2): beta = -sign(alpha) ||a|| (sign(0) = +1), y1 = alpha -
 // beta, 1 / y1 and tau = (beta - alpha) / beta (= 2 / v^T v with v = y / y1),

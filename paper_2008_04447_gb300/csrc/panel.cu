@@ -297,18 +297,6 @@ __device__ __forceinline__ void t_column(int jc, double tau, double* sT, const d
   if (threadIdx.x == 0) sT[(size_t)jc * kFB + jc] = tau;
 }
 
-// Float-float addition (Knuth's TwoSum for the high parts, the low parts
-// added with the rounding error): sums of squares of FP32 values carried to
-// about 2^-44 relative without FP64 arithmetic.  Commutative, so a butterfly
-// leaves the same bits in every lane.
-__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
-  const float s = h + bh;
-  const float bb = s - h;
-  const float err = (h - (s - bb)) + (bh - bb);
-  l = (l + bl) + err;
-  h = s;
-}
-
 template <typename TS, int TPR>
 __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a) {
   constexpr int CPT = kFB / TPR;  // columns per thread
@@ -554,7 +542,14 @@ cudaError_t panel_qr(const Ctx& c, TS* P, int ldp, int mt, int bj, TS* tau, TS* 
     // the thread-per-row kernel when the panel fits one row per thread
     constexpr int TPR = sizeof(TS) == sizeof(double) ? 2 : 1;
     constexpr int RPP = kThreads / TPR;
-    const int Gf = (mt + RPP - 1) / RPP;
+    // FP32 rows: as few CTAs as hold the panel (the step is latency-bound and
+    // fewer CTAs make cheaper reductions); FP64 rows: the FP64 pipe bounds the
+    // step, so spread the rows over every SM (down to 64 rows per CTA)
+    int Gf = (mt + RPP - 1) / RPP;
+    if (sizeof(TS) == sizeof(double)) {
+      const int g64 = (mt + 63) / 64;
+      Gf = g64 < c.num_sms ? (g64 > Gf ? g64 : Gf) : (c.num_sms > Gf ? c.num_sms : Gf);
+    }
     if (bj <= kFB && Gf <= c.num_sms && Gf <= 4 * kMaxG4) {
       static int per_sm_fast = -1;
       if (per_sm_fast < 0) {

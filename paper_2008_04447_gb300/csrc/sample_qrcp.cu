@@ -35,27 +35,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSteps = 256;
 constexpr int kMaxRecS = 8;  // candidate records per lane: G <= 256
 
-// The squared norms compared here are never negative, and for non-negative
-// doubles the IEEE order is the order of their bit patterns as integers, so
-// the argmax compares 64-bit integers (an FP64 comparison is a long-latency
-// operation on this part).  Ties go to the lowest current position; p < 0 =
-// empty.
-__device__ __forceinline__ bool better_key(long long k1, int p1, long long k2, int p2) {
-  if (p2 < 0) return p1 >= 0;
-  if (p1 < 0) return false;
-  return (k1 > k2) || (k1 == k2 && p1 < p2);
-}
-
-__device__ __forceinline__ void warp_argmax_key(long long& k, int& p, int& tag) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
-    const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
-    const int t2 = __shfl_xor_sync(0xffffffffu, tag, o);
-    if (better_key(k2, p2, k, p)) { k = k2; p = p2; tag = t2; }
-  }
-}
-
 template <typename TS>
 struct SqArgs {
   const TS* B;
