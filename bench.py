@@ -575,17 +575,22 @@ def main():
         torch.cuda.synchronize()
         eclk = Clocks(local)
         eclk.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        ev0.record()
         E = 2
         for _ in range(E):
             e2e_step()
+        ev1.record()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / E
+        e2e_dev_s = ev0.elapsed_time(ev1) / 1e3 / E
         e2e_clocks = eclk.stop()
         esz = A0.element_size()
         line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
                        "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": e2e_s,
-                       "clocks": e2e_clocks}
+                       "device_s_per_step": e2e_dev_s, "clocks": e2e_clocks}
         del Ah, Ao
 
     if "qr" in legs:
