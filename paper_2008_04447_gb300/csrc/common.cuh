@@ -104,23 +104,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// (value, position) max with ties to the lowest position; pos < 0 = empty.
-__device__ __forceinline__ bool better(double v1, int p1, double v2, int p2) {
-  if (p2 < 0) return p1 >= 0;
-  if (p1 < 0) return false;
-  return (v1 > v2) || (v1 == v2 && p1 < p2);
-}
-
-__device__ __forceinline__ void warp_argmax(double& v, int& p, int& tag) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-    int p2 = __shfl_xor_sync(0xffffffffu, p, o);
-    int t2 = __shfl_xor_sync(0xffffffffu, tag, o);
-    if (better(v2, p2, v, p)) { v = v2; p = p2; tag = t2; }
-  }
-}
-
 // Float-float addition (Knuth's TwoSum for the high parts, the low parts
 // added with the rounding error): sums of squares of FP32 values carried to
 // about 2^-44 relative without FP64 arithmetic.  Commutative, so a butterfly
