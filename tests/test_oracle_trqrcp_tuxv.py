@@ -152,3 +152,24 @@ def test_tuxv_iterations_are_subspace_iteration():
     assert all(e2 <= e1 for e1, e2 in zip(excess, excess[1:]))
     assert all(e2 <= 0.25 * e1 for e1, e2 in zip(excess[2:], excess[3:]))
     assert excess[0] > 0.1 * opt2 and excess[-1] <= 1e-9 * opt2
+
+
+def test_bf16_sketch_keeps_rank_k_error_on_a_quiet_tail():
+    """The reduced-precision reading (the sketch formed from bfloat16-rounded
+    Omega and A, everything else FP64) on the low-rank workload with a quiet
+    tail (noise 1e-10, where the rank-k error is set by the singular values
+    rather than a noise floor): the rank-k error stays within 1.05x of the
+    FP64-sketch error, and both are at least the Eckart-Young error."""
+    for seed in (3, 4):
+        a = I.lowrank_plus_noise(2048, 1024, 512, 1e-10, seed=seed)
+        om = I.omega(72, 2048, seed=seed + 100)
+        k = 128
+        s = np.linalg.svd(a, compute_uv=False)
+        nrm = np.linalg.norm(a)
+        ey = np.sqrt(np.sum(s[k:] ** 2)) / nrm
+        t64 = O.tuxv(a, om, 64, k)
+        tbf = O.tuxv(a, om, 64, k, sketch_inputs="bf16")
+        e64 = np.linalg.norm(a - t64.U @ t64.X @ t64.V.T) / nrm
+        ebf = np.linalg.norm(a - tbf.U @ tbf.X @ tbf.V.T) / nrm
+        assert ebf <= 1.05 * e64
+        assert min(e64, ebf) >= ey * (1 - 1e-10)
