@@ -1,0 +1,125 @@
+"""Host logic of the continuous-batching server (no GPU): admission against the
+HBM budget, routing of large and small requests, at most `lanes` launches in
+flight, completion and draining.  The library handle, CUDA streams and events
+are replaced by fakes that record the calls; a fake event completes when the
+test says so."""
+import contextlib
+
+import pytest
+import torch
+
+from paper_2008_04447_gb300 import serve
+
+
+class FakeHandle:
+    log = []
+
+    def tuxv(self, A, Omega, b, p, k, prec=None, stream=None):
+        FakeHandle.log.append(("tuxv", tuple(A.shape), k))
+        m, n = A.shape
+        return (torch.zeros(m, k), torch.zeros(k, k), torch.zeros(n, k), None, torch.zeros(1, dtype=torch.int32))
+
+    def tuxv_batched(self, problems, prec=None, stream=None, outputs=None):
+        FakeHandle.log.append(("batched", [tuple(t[0].shape) for t in problems]))
+        return outputs, torch.zeros(len(problems), dtype=torch.int32)
+
+
+class FakeEvent:
+    live = []
+
+    def __init__(self):
+        self.done = False
+        FakeEvent.live.append(self)
+
+    def record(self, stream=None):
+        pass
+
+    def query(self):
+        return self.done
+
+
+class FakeStream:
+    cuda_stream = 0
+
+    def __init__(self, device=None):
+        pass
+
+
+@pytest.fixture
+def fakes(monkeypatch):
+    FakeHandle.log = []
+    FakeEvent.live = []
+    monkeypatch.setattr(serve, "Handle", FakeHandle)
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    return FakeHandle.log
+
+
+def req(m, n, k=8, b=8, p=4):
+    return torch.zeros(m, n), torch.zeros(b + p, m), b, p, k
+
+
+def finish_all():
+    for e in FakeEvent.live:
+        e.done = True
+
+
+def test_oversized_request_is_rejected(fakes):
+    srv = serve.Server(budget_bytes=1e6, lanes=2, device="cpu")
+    with pytest.raises(MemoryError):
+        srv.submit(*req(2000, 1000))
+    assert srv.rejected == 1
+
+
+def test_admission_never_exceeds_the_budget(fakes):
+    one = serve.footprint_bytes(300, 200, 8, 8, 4)
+    srv = serve.Server(budget_bytes=2.5 * one, lanes=4, device="cpu")
+    rs = [srv.submit(*req(300, 200)) for _ in range(5)]
+    srv.pump()
+    assert srv.used <= srv.budget
+    assert sum(r.admitted > 0 for r in rs) == 2          # only two fit
+    finish_all()
+    srv.pump()                                            # reap frees memory, admits the next ones
+    assert srv.used <= srv.budget
+    assert sum(r.admitted > 0 for r in rs) == 4
+    for _ in range(4):
+        finish_all()
+        srv.pump()
+    assert srv.idle() and len(srv.completed) == 5 and srv.used == 0
+
+
+def test_large_requests_go_alone_to_the_single_problem_path(fakes):
+    srv = serve.Server(budget_bytes=1e12, lanes=3, large_mn=100 * 100, device="cpu")
+    small = [srv.submit(*req(64 + 8 * i, 48)) for i in range(4)]
+    big = srv.submit(*req(300, 200, k=16))
+    srv.pump()
+    kinds = [c[0] for c in fakes]
+    assert kinds.count("tuxv") == 1 and kinds.count("batched") == 1
+    batched = next(c for c in fakes if c[0] == "batched")[1]
+    assert len(batched) == 4
+    assert batched == sorted(batched, key=lambda s: -(s[0] * s[1]))   # largest first
+    assert ("tuxv", (300, 200), 16) in fakes
+    finish_all()
+    srv.pump()
+    for r in small + [big]:
+        assert r.wait(1) is not None
+
+
+def test_at_most_lanes_launches_in_flight(fakes):
+    srv = serve.Server(budget_bytes=1e12, lanes=2, large_mn=10, device="cpu")   # every request is large
+    rs = [srv.submit(*req(50, 40)) for _ in range(5)]
+    srv.pump()
+    assert len(fakes) == 2 and sum(s is not None for s in srv.busy) == 2
+    srv.pump()
+    assert len(fakes) == 2                                # nothing frees, nothing starts
+    FakeEvent.live[0].done = True
+    srv.pump()
+    assert len(fakes) == 3                                # one lane freed, one launch
+    for _ in range(5):
+        finish_all()
+        srv.pump()
+    srv.drain(timeout=1.0)
+    assert all(r.done >= r.started >= r.admitted >= r.arrival for r in rs)
+    st = srv.stats()
+    assert st["completed"] == 5
