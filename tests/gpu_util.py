@@ -47,3 +47,27 @@ def factor_quality(a, F, tau, jpvt, k):
     resid = np.linalg.norm(a[:, jpvt] - Qf @ Rf) / np.linalg.norm(a)
     orth = np.linalg.norm(Qf.T @ Qf - np.eye(m))
     return resid, orth
+
+
+def column_norm_mismatch(Fcols_r_norms, a_cols_norms):
+    """max_j | ||R(:, j)|| - ||A(:, jpvt[j])|| | / ||A(:, jpvt[j])|| (0 / 0 taken as 0).
+
+    An orthogonal transform preserves column norms, so the R of A P = Q R has
+    ||R(:, j)|| = ||A(:, jpvt[j])|| for every j, at any size."""
+    r = np.asarray(Fcols_r_norms, dtype=np.float64)
+    a = np.asarray(a_cols_norms, dtype=np.float64)
+    den = np.where(a > 0, a, 1.0)
+    return float(np.max(np.abs(r - a) / den))
+
+
+def r_column_norms(F, k):
+    """||R(:, j)|| from a packed factorisation F (R on and above the diagonal in
+    rows < k; rows >= k of columns >= k hold the trailing block R22)."""
+    F = np.asarray(F)
+    m, n = F.shape
+    out = np.empty(n)
+    for j in range(n):
+        top = F[: min(j + 1, k), j]
+        tail = F[k:, j] if j >= k else np.zeros(0)
+        out[j] = np.sqrt(np.sum(top * top) + np.sum(tail * tail))
+    return out

@@ -149,3 +149,21 @@ def test_rsrqrcp_runs_and_is_valid():
     res = O.rqrcp(a, I.omega(b + p, m, seed=14), b, mode="resample", resample=draws)
     resid, orth = _residuals(a, res)
     assert resid <= 1e-14
+
+
+def test_column_norm_property_helper_on_the_oracle():
+    """The full-size GPU check uses ||R(:, j)|| = ||A(:, jpvt[j])||; its helper is
+    pinned here on the oracle's own factorisation (and a planted error in R)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from gpu_util import column_norm_mismatch, r_column_norms
+    a = I.graded(300, 240, 8, seed=5)
+    for k in (None, 100):
+        res = O.rqrcp(a, I.omega(40, 300, seed=6), 32, k)
+        kk = res.k
+        rn = r_column_norms(res.F, kk)
+        an = np.linalg.norm(a, axis=0)[res.jpvt]
+        assert column_norm_mismatch(rn, an) <= 1e-13
+        F = res.F.copy()
+        F[3, 50] *= 1.001                       # planted error in one R entry
+        assert column_norm_mismatch(r_column_norms(F, kk), an) > 1e-7
