@@ -43,8 +43,10 @@ extern "C" {
 
 /* Arithmetic / storage precision of a call. */
 #define RQ_FP64 0  /* everything FP64 */
-#define RQ_FP32 1  /* FP32 storage and updates; Householder vectors, tau, norms in FP64 */
-#define RQ_MIXED 2 /* FP32 storage, BF16 sketch, FP32 updates; FP64 reflectors, norms, core SVD */
+#define RQ_FP32 1  /* FP32 storage and updates (3xTF32 tensor-core products); the Householder
+                      scalars, T and squared norms carried with FP64 accuracy */
+#define RQ_MIXED 2 /* as RQ_FP32, with the sketch formed from bfloat16-rounded Omega and A
+                      (FP32 accumulation); core SVD in FP64 */
 
 /* Operations, for rq_workspace_size. */
 #define RQ_OP_RQRCP 0
