@@ -3,6 +3,7 @@
 // Everything a call does is issued asynchronously on the caller's stream; the
 // host never waits on the device inside rqrcp/qr (pivots, the sample and the
 // reflectors stay on the GPU between blocks).
+#include <nvtx3/nvToolsExt.h>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -77,6 +78,12 @@ int next_event(rq_handle h) {
 
 // Records CUDA events around one phase on the call's stream (when profiling),
 // and accounts the phase's algorithmic flops / bytes.
+// Each phase is also an NVTX range (header-only NVTX v3: a no-op unless a
+// profiling tool is attached), so timeline tools show the path's phases.
+const char* const kPhaseNames[RQ_NUM_PHASES] = {"rq sketch",         "rq sample QRCP",    "rq permute",
+                                                "rq panel",          "rq trailing update", "rq sample update",
+                                                "rq other"};
+
 struct Phase {
   rq_handle h;
   cudaStream_t st;
@@ -84,6 +91,7 @@ struct Phase {
   long long l0;
   Phase(rq_handle h_, cudaStream_t st_, int ph, double flops, double bytes)
       : h(h_), st(st_), phase(ph), ev0(-1), l0(h_->launches) {
+    nvtxRangePushA(kPhaseNames[ph]);
     if (!h->prof_on) return;
     ev0 = next_event(h);
     if (ev0 >= 0) cudaEventRecord(h->ev_pool[ev0], st);
@@ -91,6 +99,7 @@ struct Phase {
     h->prof_bytes[ph] += bytes;
   }
   ~Phase() {
+    nvtxRangePop();
     if (!h->prof_on || ev0 < 0) return;
     int ev1 = next_event(h);
     if (ev1 < 0) return;
