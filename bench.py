@@ -557,114 +557,142 @@ def main():
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     legs = args.legs if rank == 0 else set()
     if "e2e" in legs:
-        # end to end through the C ABI with host buffers (pinned; column-major A is
-        # copied as its contiguous transpose so each copy is one cudaMemcpyAsync)
-        Ah = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
-        Ah.copy_(A0.t())
-        Ao = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
-        tau_h = torch.empty(n, dtype=A0.dtype, pin_memory=True)
-        jp_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        try:
+            # end to end through the C ABI with host buffers (pinned; column-major A is
+            # copied as its contiguous transpose so each copy is one cudaMemcpyAsync)
+            Ah = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
+            Ah.copy_(A0.t())
+            Ao = torch.empty((n, m), dtype=A0.dtype, pin_memory=True)
+            tau_h = torch.empty(n, dtype=A0.dtype, pin_memory=True)
+            jp_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
 
-        def e2e_step():
-            A.t().copy_(Ah, non_blocking=True)
-            tau, jpvt, info = h.rqrcp(A, Om, b, p)
-            Ao.copy_(A.t(), non_blocking=True)
-            tau_h.copy_(tau, non_blocking=True)
-            jp_h.copy_(jpvt, non_blocking=True)
-        e2e_step()
-        torch.cuda.synchronize()
-        eclk = Clocks(local)
-        eclk.start()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
-        ev0.record()
-        E = 2
-        for _ in range(E):
+            def e2e_step():
+                A.t().copy_(Ah, non_blocking=True)
+                tau, jpvt, info = h.rqrcp(A, Om, b, p)
+                Ao.copy_(A.t(), non_blocking=True)
+                tau_h.copy_(tau, non_blocking=True)
+                jp_h.copy_(jpvt, non_blocking=True)
             e2e_step()
-        ev1.record()
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / E
-        e2e_dev_s = ev0.elapsed_time(ev1) / 1e3 / E
-        e2e_clocks = eclk.stop()
-        esz = A0.element_size()
-        line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
-                       "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": e2e_s,
-                       "device_s_per_step": e2e_dev_s, "clocks": e2e_clocks}
-        del Ah, Ao
+            torch.cuda.synchronize()
+            eclk = Clocks(local)
+            eclk.start()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            ev0.record()
+            E = 2
+            for _ in range(E):
+                e2e_step()
+            ev1.record()
+            torch.cuda.synchronize()
+            e2e_s = (time.perf_counter() - t0) / E
+            e2e_dev_s = ev0.elapsed_time(ev1) / 1e3 / E
+            e2e_clocks = eclk.stop()
+            esz = A0.element_size()
+            line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
+                           "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": e2e_s,
+                           "device_s_per_step": e2e_dev_s, "clocks": e2e_clocks}
+            del Ah, Ao
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["e2e"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
 
     if "qr" in legs:
-        # unpivoted blocked QR of the same matrix, same kernels (the paper's comparison)
-        def qr_step():
-            A.copy_(A0)
-            h.qr(A, b)
-        qr_step()
-        torch.cuda.synchronize()
-        qclk = Clocks(local)
-        qclk.start()
-        q0 = torch.cuda.Event(enable_timing=True)
-        q1 = torch.cuda.Event(enable_timing=True)
-        q0.record()
-        for _ in range(2):
+        try:
+            # unpivoted blocked QR of the same matrix, same kernels (the paper's comparison)
+            def qr_step():
+                A.copy_(A0)
+                h.qr(A, b)
             qr_step()
-        q1.record()
-        torch.cuda.synchronize()
-        qr_ms = q0.elapsed_time(q1) / 2
-        line["qr"] = {"s": qr_ms / 1e3, "tflops": fl / (qr_ms / 1e3) / 1e12,
-                      "rqrcp_over_qr": ms_step / qr_ms, "clocks": qclk.stop()}
+            torch.cuda.synchronize()
+            qclk = Clocks(local)
+            qclk.start()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record()
+            for _ in range(2):
+                qr_step()
+            q1.record()
+            torch.cuda.synchronize()
+            qr_ms = q0.elapsed_time(q1) / 2
+            line["qr"] = {"s": qr_ms / 1e3, "tflops": fl / (qr_ms / 1e3) / 1e12,
+                          "rqrcp_over_qr": ms_step / qr_ms, "clocks": qclk.stop()}
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["qr"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
 
     if "fp32" in legs and args.prec == "fp64":
-        # FP32 path on the same matrix (FP32 storage and updates, FP64 reflectors and norms)
-        A32 = A0.float()
-        A32 = colmajor(A32)
-        Om32 = colmajor(Om.float())
-        W = torch.empty_like(A32)
+        try:
+            # FP32 path on the same matrix (FP32 storage and updates, FP64 reflectors and norms)
+            A32 = A0.float()
+            A32 = colmajor(A32)
+            Om32 = colmajor(Om.float())
+            W = torch.empty_like(A32)
 
-        def f32(fn):
-            W.copy_(A32)
-            fn()
-        for _ in range(2):
-            f32(lambda: h.rqrcp(W, Om32, b, p))
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record()
-        for _ in range(3):
-            f32(lambda: h.rqrcp(W, Om32, b, p))
-        g1.record()
-        torch.cuda.synchronize()
-        r32 = g0.elapsed_time(g1) / 3
-        f32(lambda: h.qr(W, b))
-        g0.record()
-        for _ in range(3):
+            def f32(fn):
+                W.copy_(A32)
+                fn()
+            for _ in range(2):
+                f32(lambda: h.rqrcp(W, Om32, b, p))
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record()
+            for _ in range(3):
+                f32(lambda: h.rqrcp(W, Om32, b, p))
+            g1.record()
+            torch.cuda.synchronize()
+            r32 = g0.elapsed_time(g1) / 3
             f32(lambda: h.qr(W, b))
-        g1.record()
-        torch.cuda.synchronize()
-        q32 = g0.elapsed_time(g1) / 3
-        line["fp32"] = {"rqrcp_s": r32 / 1e3, "rqrcp_tflops": fl / (r32 / 1e3) / 1e12, "qr_s": q32 / 1e3,
-                        "qr_tflops": fl / (q32 / 1e3) / 1e12, "rqrcp_over_qr": r32 / q32}
-        del A32, W
+            g0.record()
+            for _ in range(3):
+                f32(lambda: h.qr(W, b))
+            g1.record()
+            torch.cuda.synchronize()
+            q32 = g0.elapsed_time(g1) / 3
+            line["fp32"] = {"rqrcp_s": r32 / 1e3, "rqrcp_tflops": fl / (r32 / 1e3) / 1e12, "qr_s": q32 / 1e3,
+                            "qr_tflops": fl / (q32 / 1e3) / 1e12, "rqrcp_over_qr": r32 / q32}
+            del A32, W
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["fp32"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
 
     if "rsrqrcp" in legs:
-        # ablation of the sample update (Sec. 3.4): repeated sampling re-sketches the
-        # trailing matrix with fresh device draws at every block; same matrix
-        line["rsrqrcp"] = leg_rsrqrcp(h, A0, A, Om, b, p, fl, ms_step, args.prec)
+        try:
+            # ablation of the sample update (Sec. 3.4): repeated sampling re-sketches the
+            # trailing matrix with fresh device draws at every block; same matrix
+            line["rsrqrcp"] = leg_rsrqrcp(h, A0, A, Om, b, p, fl, ms_step, args.prec)
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["rsrqrcp"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
 
     if "cpu" in legs:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_n, b, p, args.decades)
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_n, b, p, args.decades)
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
     del A0, A
     torch.cuda.empty_cache()
     if "tuxv" in legs:
-        line["tuxv"] = leg_tuxv(h)
-        torch.cuda.empty_cache()
+        try:
+            line["tuxv"] = leg_tuxv(h)
+            torch.cuda.empty_cache()
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["tuxv"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
     if "batched" in legs or "serving" in legs:
-        host = batch_inputs(args.batch, seed=0)
-        dev = to_device_f32(host)
-        if "batched" in legs:
-            line["batched"] = leg_batched(h, host, dev)
-        if "serving" in legs:
-            line["serving"] = leg_serving(dev)
-        del dev
+        try:
+            host = batch_inputs(args.batch, seed=0)
+            dev = to_device_f32(host)
+            if "batched" in legs:
+                line["batched"] = leg_batched(h, host, dev)
+            if "serving" in legs:
+                line["serving"] = leg_serving(dev)
+            del dev
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["batched+serving"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
     barrier(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
