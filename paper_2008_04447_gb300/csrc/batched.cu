@@ -172,8 +172,9 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
   for (int e = tid; e < bj * bj; e += NT) T[(e % bj) + (size_t)(e / bj) * ldt] = 0.0;
   for (int j = 0; j < bj; ++j) {
     float* aj = P + (size_t)j * ldp;
-    // squared norm below row j with FP64 accuracy: float-float per thread and
-    // warp (FP64 for a warp holding an entry outside [2^-60, 2^55]), combined
+    // squared norm below row j: float-float per thread and warp (FP64 for a
+    // warp holding an entry outside [2^-60, 2^55]; about 2^-44 relative for
+    // entries of at least 2^-38, toward FP32's accuracy below that), combined
     // in FP64 by thread 0, which forms the reflector's scalars (FP64 is slow
     // on this part, so it stays off the all-thread path)
     {
@@ -293,8 +294,9 @@ __device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, doubl
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double tol = 3.4526698300124393e-04;  // sqrt(FLT_EPSILON): the sample is held in FP32
   for (int c = tid; c < nt; c += NT) {
-    // squared column norm with FP64 accuracy in float-float arithmetic (FP64
-    // when an entry lies outside [2^-60, 2^55])
+    // squared column norm in float-float arithmetic (FP64 when an entry lies
+    // outside [2^-60, 2^55]; about 2^-44 relative for entries of at least
+    // 2^-38, toward FP32's accuracy below that)
     const float* bc = B + (size_t)c * l;
     float h = 0.f, lo = 0.f;
     bool oor = false;
