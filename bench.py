@@ -337,15 +337,27 @@ def leg_tuxv(h, steps=3, warmup=3, shape=(32768, 16384, 512)):
     return out
 
 
-def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24):
-    """4096 uneven problems in one persistent launch (mixed precision)."""
+def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24, tune=True):
+    """4096 uneven problems in one persistent launch (mixed precision).
+
+    With tune, the tile policy is autotuned on the batch first (outside the
+    timed region; every policy gives the same bits)."""
     import numpy as np
     import torch
     import oracle as O
     from paper_2008_04447_gb300 import RQ_MIXED
     order = sorted(range(len(dev)), key=lambda i: -(dev[i][0].shape[0] * dev[i][0].shape[1] * dev[i][4]))
     probs = [dev[i] for i in order]
-    outs, info = h.tuxv_batched(probs, prec=RQ_MIXED)
+    tuning = {"tiles": list(h.batch_tiles)}
+    outs = None
+    if tune:
+        try:
+            t0 = time.perf_counter()
+            tiles, tuned_ms, outs, _ = h.tune_batched(probs, prec=RQ_MIXED, reps=1, passes=2)
+            tuning = {"tiles": list(tiles), "tune_s": time.perf_counter() - t0, "tuned_ms": tuned_ms}
+        except Exception as exc:  # the policy stays as it was; the leg is still measured
+            tuning["tune_error"] = f"{type(exc).__name__}: {exc}"[:200]
+    outs, info = h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
     for _ in range(warmup - 1):
         h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
     torch.cuda.synchronize()
@@ -372,13 +384,15 @@ def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24):
         ratios.append(e_gpu / e_ref)
     return {"workload": f"batched_tuxv_mixed_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
             "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
-            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "info_nonzero": int((info != 0).sum()),
+            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "info_nonzero": int((info != 0).sum()), **tuning,
             "error_ratio_vs_fp64_oracle": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
                                            "max": float(np.max(ratios)) if ratios else None}}
 
 
-def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9):
-    """Poisson arrivals of TUXV requests: the batch mix plus 10% 8192 x 4096, k = 256."""
+def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9,
+                tiles=None):
+    """Poisson arrivals of TUXV requests: the batch mix plus 10% 8192 x 4096, k = 256
+    (tiles: the batched kernel's tile policy for the server's lanes)."""
     import numpy as np
     import torch
     from paper_2008_04447_gb300 import colmajor
@@ -395,7 +409,7 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
     old_switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)
     for rate in rates:
-        srv = Server(budget_bytes=budget, lanes=3)
+        srv = Server(budget_bytes=budget, lanes=3, tiles=tiles)
         # warm the lanes' workspaces
         for lane_h, st in srv.lanes:
             lane_h.tuxv_batched(dev[:8], stream=st)
@@ -688,7 +702,7 @@ def main():
             if "batched" in legs:
                 line["batched"] = leg_batched(h, host, dev)
             if "serving" in legs:
-                line["serving"] = leg_serving(dev)
+                line["serving"] = leg_serving(dev, tiles=line.get("batched", {}).get("tiles"))
             del dev
         except Exception as exc:  # a failing extra leg must not lose the headline line
             line["batched+serving"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}

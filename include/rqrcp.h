@@ -15,8 +15,10 @@
  * - Element type follows `prec`: RQ_FP64 -> double, RQ_FP32 and RQ_MIXED ->
  *   float (A, Omega, tau, R, Y, U, X, V, sigma).  Index vectors are int32.
  * - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
- *   stream).  The return value reports argument / launch problems found on
- *   the host; numerical status is written to the caller's device `info` word.
+ *   stream); rq_profile_read and rq_tune_batched synchronise, as their
+ *   comments say.  The return value reports argument / launch problems found
+ *   on the host; numerical status is written to the caller's device `info`
+ *   word.
  * - The library owns only its workspace, held in the handle (see
  *   rq_workspace_size / rq_set_workspace).  No exception crosses the ABI.
  *
@@ -294,6 +296,73 @@ typedef struct rq_problem {
  */
 int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,
                     int max_b, int max_p, rq_stream stream);
+
+/*
+ * Tile policy of rq_tuxv_batched's block-level FP32 products.  A product with
+ * M output rows and N output columns runs on 32 x 128 tiles when
+ * M <= skinny_m, else on 128 x 32 tiles when N <= skinny_n, else on 64 x 64
+ * tiles.  Every tile shape accumulates each output over the inner dimension
+ * in the same order with the same operations, so the policy changes the speed
+ * only: the results are the same bit for bit under every policy.  A new handle
+ * holds {32, 32}.
+ */
+typedef struct rq_batch_tiles {
+  int skinny_m; /* >= 0 */
+  int skinny_n; /* >= 0 */
+} rq_batch_tiles;
+
+/*
+ * rq_set_batch_tiles / rq_get_batch_tiles -- the handle's policy, used by its
+ * later rq_tuxv_batched calls (a call captured in a CUDA graph keeps the
+ * policy it was captured with).  t NULL or a negative threshold -> -2.
+ */
+int rq_set_batch_tiles(rq_handle h, const rq_batch_tiles* t);
+int rq_get_batch_tiles(rq_handle h, rq_batch_tiles* t);
+
+/*
+ * Cost of one policy for rq_tiles_search: writes a time (any unit; finite and
+ * >= 0) to *ms and returns 0.  A non-zero return ends the search with that
+ * status.
+ */
+typedef int (*rq_tiles_measure)(void* user, const rq_batch_tiles* tiles, double* ms);
+
+/* The values each threshold takes in the search. */
+#define RQ_TILE_STEPS 6 /* 0, 16, 32, 64, 128, 256 */
+
+/*
+ * rq_tiles_search -- the autotuner's search; host only, no CUDA call.
+ * Coordinate descent over the two thresholds: from `start` (NULL: {32, 32}),
+ * a pass tries every other value of skinny_m, then every other value of
+ * skinny_n, and moves to a candidate only when its time is below 0.99 x the
+ * incumbent's (so timing noise does not move it).  The search stops after a
+ * pass that moves nothing, or after `passes` passes; no policy is measured
+ * twice.
+ *   measure, user  the cost function and its context pointer.
+ *   start          nullable; thresholds >= 0.
+ *   passes         >= 0; 0 measures `start` alone.
+ *   best           out: the chosen policy.  best_ms (nullable): its time.
+ * Returns 0; -1 if measure is NULL or gives a time that is not finite and
+ * >= 0; -3 for a negative threshold in start; -4 for passes < 0; -5 if best
+ * is NULL; else the measure's own non-zero status.
+ */
+int rq_tiles_search(rq_tiles_measure measure, void* user, const rq_batch_tiles* start, int passes,
+                    rq_batch_tiles* best, double* best_ms);
+
+/*
+ * rq_tune_batched -- autotunes the handle's tile policy on a batch.  Arguments
+ * 1-9 as rq_tuxv_batched.  It runs the batch once to warm up, then
+ * rq_tiles_search from the handle's current policy, measuring a policy as the
+ * fastest of `reps` launches (CUDA events on `stream`), and stores the chosen
+ * policy in the handle.  It synchronises the stream, so it cannot be captured
+ * in a CUDA graph.  The outputs hold the batch's result afterwards (every
+ * policy gives the same bits).
+ *   reps    >= 1 (argument 10).      passes  >= 0 (argument 11).
+ *   best    nullable: the chosen policy.  best_ms (nullable): its time in ms.
+ * On an error the handle's policy is left as it was.
+ */
+int rq_tune_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,
+                    int max_b, int max_p, int reps, int passes, rq_stream stream, rq_batch_tiles* best,
+                    double* best_ms);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_
                    RQ_OP_TUXV, rq_create, rq_destroy, rq_last_error, rq_launch_count, rq_profile_enable,
                    rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp,
                    rq_tuxv, rq_tuxv_batched, rq_tuxv_iter, rq_latent_cdf, rq_padding,
-                   rq_workspace_size)
+                   rq_workspace_size, rq_set_batch_tiles, rq_get_batch_tiles, rq_tiles_search, rq_tune_batched)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
 
@@ -143,6 +143,39 @@ class Handle:
         every problem: [(U, X = diag(sigma), V, sigma), ...]) and the info tensor.
         The descriptors are built on the host and copied to the device.
         """
+        outputs, info, d, bounds = self._batch(problems, outputs, svd)
+        rc = rq_tuxv_batched(self.h, prec, len(problems), d, *bounds, stream)
+        self._check(rc, "rq_tuxv_batched")
+        self._keep = d  # the descriptors must outlive the asynchronous launch
+        return outputs, info
+
+    def tune_batched(self, problems, prec=RQ_MIXED, reps=2, passes=2, stream=None, outputs=None, svd=False):
+        """Autotunes the batched kernel's tile policy on these problems (synchronous).
+
+        Returns ((skinny_m, skinny_n), ms, outputs, info): the policy now held by
+        the handle, the batch's time under it, and the batch's result (the same
+        bits under every policy).
+        """
+        outputs, info, d, bounds = self._batch(problems, outputs, svd)
+        rc, tiles, ms = _lib.rq_tune_batched(self.h, prec, len(problems), d, *bounds, reps, passes, stream)
+        self._check(rc, "rq_tune_batched")
+        return tiles, ms, outputs, info
+
+    @property
+    def batch_tiles(self):
+        """(skinny_m, skinny_n): the tile policy of later batched calls."""
+        rc, t = _lib.rq_get_batch_tiles(self.h)
+        self._check(rc, "rq_get_batch_tiles")
+        return t
+
+    @batch_tiles.setter
+    def batch_tiles(self, t):
+        self._check(_lib.rq_set_batch_tiles(self.h, int(t[0]), int(t[1])), "rq_set_batch_tiles")
+
+    @staticmethod
+    def _batch(problems, outputs, svd):
+        """Outputs (allocated unless given), info, the device descriptor array
+        and the bounds (max m, n, k, b, p) of a batched call."""
         import numpy as np
         import torch
         dev = problems[0][0].device
@@ -168,10 +201,7 @@ class Handle:
         mk = max(int(t[4]) for t in problems)
         mb = max(int(t[2]) for t in problems)
         mp = max(int(t[3]) for t in problems)
-        rc = rq_tuxv_batched(self.h, prec, len(problems), d, mm, mn, mk, mb, mp, stream)
-        self._check(rc, "rq_tuxv_batched")
-        self._keep = d  # the descriptors must outlive the asynchronous launch
-        return outputs, info
+        return outputs, info, d, (mm, mn, mk, mb, mp)
 
     def gaussian(self, l, m, seed, substream=0, dtype=None, out=None, stream=None):
         """l x m column-major Gaussian draws of (seed, substream) (Sec. 3.1's Omega)."""

@@ -31,6 +31,16 @@ PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing", "sample_updat
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
+
+
+class rq_batch_tiles(ctypes.Structure):
+    """Tile policy of the batched kernel's block GEMMs (two int32 thresholds)."""
+    _fields_ = [("skinny_m", ctypes.c_int), ("skinny_n", ctypes.c_int)]
+
+
+# int (*rq_tiles_measure)(void* user, const rq_batch_tiles* tiles, double* ms)
+rq_tiles_measure = ctypes.CFUNCTYPE(_I, _P, ctypes.POINTER(rq_batch_tiles), ctypes.POINTER(ctypes.c_double))
+RQ_TILE_STEPS = (0, 16, 32, 64, 128, 256)
 _SIGS = {
     "rq_create": ([ctypes.POINTER(_P)], _I),
     "rq_destroy": ([_P], _I),
@@ -47,6 +57,12 @@ _SIGS = {
     "rq_tuxv": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_iter": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
+    "rq_set_batch_tiles": ([_P, ctypes.POINTER(rq_batch_tiles)], _I),
+    "rq_get_batch_tiles": ([_P, ctypes.POINTER(rq_batch_tiles)], _I),
+    "rq_tiles_search": ([rq_tiles_measure, _P, ctypes.POINTER(rq_batch_tiles), _I, ctypes.POINTER(rq_batch_tiles),
+                         ctypes.POINTER(ctypes.c_double)], _I),
+    "rq_tune_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _I, _I, _P, ctypes.POINTER(rq_batch_tiles),
+                         ctypes.POINTER(ctypes.c_double)], _I),
     "rq_rsrqrcp": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, ctypes.c_uint64, _P, _P, _P, _P], _I),
     "rq_latent_cdf": ([_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], _I),
     "rq_padding": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], _I),
@@ -168,6 +184,52 @@ def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, s
 
 def rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, stream=None):
     return load().rq_tuxv_batched(h, prec, count, _ptr(problems), max_m, max_n, max_k, max_b, max_p, _stream(stream))
+
+
+def rq_set_batch_tiles(h, skinny_m, skinny_n):
+    return load().rq_set_batch_tiles(h, ctypes.byref(rq_batch_tiles(skinny_m, skinny_n)))
+
+
+def rq_get_batch_tiles(h):
+    """(status, (skinny_m, skinny_n)) of the handle's tile policy."""
+    t = rq_batch_tiles()
+    rc = load().rq_get_batch_tiles(h, ctypes.byref(t))
+    return rc, (t.skinny_m, t.skinny_n)
+
+
+def rq_tiles_search(measure, start=None, passes=2):
+    """The autotuner's search with a Python cost function ``measure((m, n)) -> ms``.
+
+    Returns (status, (skinny_m, skinny_n), ms).  An exception raised by
+    ``measure`` ends the search and is re-raised here.
+    """
+    err = []
+
+    def cb(_user, tiles, ms):
+        try:
+            ms[0] = float(measure((tiles.contents.skinny_m, tiles.contents.skinny_n)))
+            return 0
+        except Exception as e:  # re-raised below, after the C search has returned
+            err.append(e)
+            return -1001
+
+    fn = rq_tiles_measure(cb)
+    best = rq_batch_tiles()
+    best_ms = ctypes.c_double()
+    st = ctypes.byref(rq_batch_tiles(*start)) if start is not None else None
+    rc = load().rq_tiles_search(fn, None, st, passes, ctypes.byref(best), ctypes.byref(best_ms))
+    if err:
+        raise err[0]
+    return rc, (best.skinny_m, best.skinny_n), best_ms.value
+
+
+def rq_tune_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, reps=2, passes=2, stream=None):
+    """(status, (skinny_m, skinny_n), ms): autotunes the handle's tile policy on a batch."""
+    best = rq_batch_tiles()
+    best_ms = ctypes.c_double()
+    rc = load().rq_tune_batched(h, prec, count, _ptr(problems), max_m, max_n, max_k, max_b, max_p, reps, passes,
+                                _stream(stream), ctypes.byref(best), ctypes.byref(best_ms))
+    return rc, (best.skinny_m, best.skinny_n), best_ms.value
 
 
 def rq_rsrqrcp(h, prec, m, n, A, lda, b, p, k, seed, tau, jpvt, info, stream=None):

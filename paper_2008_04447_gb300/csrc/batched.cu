@@ -136,14 +136,21 @@ __device__ void bgemm(int M, int N, int K, float alpha, const float* A, int lda,
   __syncthreads();
 }
 
-// Dispatch on the output shape: skinny outputs use 32 x 128 tiles.
+// The launch's tile policy, copied into shared memory by the kernel's first
+// threads (every CTA reads the same two values, so the dispatch is uniform).
+__shared__ int s_skinny_m, s_skinny_n;
+
+// Dispatch on the output shape and the tile policy: 32 x 128 tiles when
+// M <= skinny_m, else 128 x 32 tiles when N <= skinny_n, else 64 x 64.  Every
+// tile shape accumulates each output over K in the same order with the same
+// FMAs, so the policy changes the speed, never a bit of C.
 template <bool TA, bool TB, bool BF16 = false>
 __device__ void gemm_b(int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb, float beta,
                        float* C, int ldc, float* sm) {
   if (M <= 0 || N <= 0) return;
-  if (M <= 32)
+  if (M <= s_skinny_m)
     bgemm<TA, TB, 32, 128, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
-  else if (N <= 32)
+  else if (N <= s_skinny_n)
     bgemm<TA, TB, 128, 32, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
   else
     bgemm<TA, TB, 64, 64, BF16>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
@@ -527,6 +534,7 @@ struct BatchArgs {
   size_t slot_bytes;
   int* counter;
   int mixed;
+  int skinny_m, skinny_n;  // tile policy of the block GEMMs (gemm_b)
 };
 
 __device__ void solve_one(const rq_problem& pr, Slot& w, Shm& s, float* sm, bool mixed) {
@@ -779,6 +787,10 @@ __global__ void __launch_bounds__(NT) tuxv_batched_kernel(BatchArgs a) {
   __shared__ Shm s;
   __shared__ int s_idx;
   char* base = a.ws + (size_t)blockIdx.x * a.slot_bytes;
+  if (threadIdx.x == 0) {
+    s_skinny_m = a.skinny_m;
+    s_skinny_n = a.skinny_n;
+  }
   while (true) {
     if (threadIdx.x == 0) s_idx = atomicAdd(a.counter, 1);
     __syncthreads();
@@ -831,12 +843,12 @@ int batched_ctas_per_sm() {
 }
 
 cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
-                         int* counter, bool mixed) {
+                         int* counter, bool mixed, int skinny_m, int skinny_n) {
   const size_t smem = kBatchSmem;
   if (batched_ctas_per_sm() < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
   if (e != cudaSuccess) return e;
-  BatchArgs a{problems, count, ws, slot_bytes, counter, mixed ? 1 : 0};
+  BatchArgs a{problems, count, ws, slot_bytes, counter, mixed ? 1 : 0, skinny_m, skinny_n};
   tuxv_batched_kernel<<<slots, NT, smem, c.stream>>>(a);
   ++*c.launches;
   return cudaGetLastError();

@@ -125,8 +125,9 @@ cudaError_t set_diag(const Ctx& c, int k, const TS* s, TS* X, int ldx);
 size_t batched_slot_bytes(int max_m, int max_n, int max_k, int max_b, int max_p);
 int batched_limits_ok(int max_b, int max_p);
 int batched_slots(int num_sms);
+// skinny_m, skinny_n: the block GEMMs' tile policy (rq_batch_tiles).
 cudaError_t tuxv_batched(const Ctx& c, int count, const rq_problem* problems, char* ws, size_t slot_bytes, int slots,
-                         int* counter, bool mixed);
+                         int* counter, bool mixed, int skinny_m, int skinny_n);
 
 cudaError_t iota(const Ctx& c, int* v, int n);
 

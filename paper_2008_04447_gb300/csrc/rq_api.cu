@@ -4,6 +4,7 @@
 // host never waits on the device inside rqrcp/qr (pivots, the sample and the
 // reflectors stay on the GPU between blocks).
 #include <nvtx3/nvToolsExt.h>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -27,6 +28,8 @@ struct rq_handle_s {
   bool ws_owned;
   long long launches;
   char last_error[256];
+  // tile policy of the batched kernel's block GEMMs (rq_batch_tiles)
+  int tile_m, tile_n;
   // per-phase timing (rq_profile_enable)
   bool prof_on;
   std::vector<cudaEvent_t> ev_pool;
@@ -40,6 +43,7 @@ namespace rq {
 namespace {
 
 constexpr int kMagic = 0x52515243;
+constexpr int kDefaultTile = 32;  // rq_batch_tiles of a new handle
 
 struct Carver {
   char* base;
@@ -653,6 +657,67 @@ int check_common(rq_handle h, int prec) {
   return RQ_OK;
 }
 
+// ---- tile autotuner of the batched kernel ---------------------------------
+
+constexpr int kTileSteps[RQ_TILE_STEPS] = {0, 16, 32, 64, 128, 256};
+constexpr double kTileMargin = 0.99;  // a candidate must beat the incumbent by 1 %
+
+struct TilePoint {
+  int m, n;
+  double ms;
+};
+
+// Time of the policy (m, n): from the memo, else from the caller's measure.
+int tile_cost(rq_tiles_measure measure, void* user, std::vector<TilePoint>& memo, int m, int n, double* ms) {
+  for (const TilePoint& p : memo)
+    if (p.m == m && p.n == n) {
+      *ms = p.ms;
+      return RQ_OK;
+    }
+  const rq_batch_tiles t{m, n};
+  double v = -1.0;
+  const int rc = measure(user, &t, &v);
+  if (rc != 0) return rc;
+  if (!std::isfinite(v) || v < 0.0) return -1;
+  memo.push_back({m, n, v});
+  *ms = v;
+  return RQ_OK;
+}
+
+// rq_tune_batched's measure: the fastest of `reps` launches of the batch
+// under the policy, by CUDA events on the call's stream.
+struct TuneCtx {
+  rq_handle h;
+  int prec, count;
+  const rq_problem* problems;
+  int max_m, max_n, max_k, max_b, max_p, reps;
+  rq_stream stream;
+  cudaEvent_t e0, e1;
+};
+
+int tune_measure(void* user, const rq_batch_tiles* t, double* ms) {
+  TuneCtx& c = *static_cast<TuneCtx*>(user);
+  c.h->tile_m = t->skinny_m;
+  c.h->tile_n = t->skinny_n;
+  const cudaStream_t st = static_cast<cudaStream_t>(c.stream);
+  double fastest = -1.0;
+  for (int r = 0; r < c.reps; ++r) {
+    cudaError_t e = cudaEventRecord(c.e0, st);
+    if (e != cudaSuccess) return cuda_fail(c.h, e, "rq_tune_batched: event");
+    const int rc = rq_tuxv_batched(c.h, c.prec, c.count, c.problems, c.max_m, c.max_n, c.max_k, c.max_b, c.max_p,
+                                   c.stream);
+    if (rc != RQ_OK) return rc;
+    float v = 0.f;
+    e = cudaEventRecord(c.e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(c.e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&v, c.e0, c.e1);
+    if (e != cudaSuccess) return cuda_fail(c.h, e, "rq_tune_batched: timing");
+    if (fastest < 0.0 || v < fastest) fastest = v;
+  }
+  *ms = fastest;
+  return RQ_OK;
+}
+
 }  // namespace
 }  // namespace rq
 
@@ -676,6 +741,8 @@ int rq_create(rq_handle* out) {
   h->ws_owned = false;
   h->launches = 0;
   h->last_error[0] = 0;
+  h->tile_m = kDefaultTile;
+  h->tile_n = kDefaultTile;
   h->prof_on = false;
   h->ev_used = 0;
   for (int i = 0; i < RQ_NUM_PHASES; ++i) h->prof_flops[i] = h->prof_bytes[i] = 0.0;
@@ -987,9 +1054,98 @@ int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems
   cudaError_t e;
   {
     Phase ph(h, c.stream, RQ_PHASE_OTHER, 0.0, 0.0);
-    e = tuxv_batched(c, count, problems, base + 256, slot, slots, counter, prec == RQ_MIXED);
+    e = tuxv_batched(c, count, problems, base + 256, slot, slots, counter, prec == RQ_MIXED, h->tile_m, h->tile_n);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rq_tuxv_batched");
+  return RQ_OK;
+}
+
+int rq_set_batch_tiles(rq_handle h, const rq_batch_tiles* t) {
+  if (!valid(h)) return RQ_EHANDLE;
+  if (!t || t->skinny_m < 0 || t->skinny_n < 0) return -2;
+  h->tile_m = t->skinny_m;
+  h->tile_n = t->skinny_n;
+  return RQ_OK;
+}
+
+int rq_get_batch_tiles(rq_handle h, rq_batch_tiles* t) {
+  if (!valid(h)) return RQ_EHANDLE;
+  if (!t) return -2;
+  t->skinny_m = h->tile_m;
+  t->skinny_n = h->tile_n;
+  return RQ_OK;
+}
+
+int rq_tiles_search(rq_tiles_measure measure, void* user, const rq_batch_tiles* start, int passes,
+                    rq_batch_tiles* best, double* best_ms) {
+  if (!measure) return -1;
+  if (start && (start->skinny_m < 0 || start->skinny_n < 0)) return -3;
+  if (passes < 0) return -4;
+  if (!best) return -5;
+  std::vector<TilePoint> memo;
+  int cur[2] = {start ? start->skinny_m : kDefaultTile, start ? start->skinny_n : kDefaultTile};
+  double cur_ms = 0.0;
+  int rc = tile_cost(measure, user, memo, cur[0], cur[1], &cur_ms);
+  if (rc != RQ_OK) return rc;
+  for (int pass = 0; pass < passes; ++pass) {
+    bool moved = false;
+    for (int axis = 0; axis < 2; ++axis) {
+      for (int v : kTileSteps) {
+        if (v == cur[axis]) continue;
+        int cand[2] = {cur[0], cur[1]};
+        cand[axis] = v;
+        double ms = 0.0;
+        rc = tile_cost(measure, user, memo, cand[0], cand[1], &ms);
+        if (rc != RQ_OK) return rc;
+        if (ms < kTileMargin * cur_ms) {
+          cur[0] = cand[0];
+          cur[1] = cand[1];
+          cur_ms = ms;
+          moved = true;
+        }
+      }
+    }
+    if (!moved) break;
+  }
+  best->skinny_m = cur[0];
+  best->skinny_n = cur[1];
+  if (best_ms) *best_ms = cur_ms;
+  return RQ_OK;
+}
+
+int rq_tune_batched(rq_handle h, int prec, int count, const rq_problem* problems, int max_m, int max_n, int max_k,
+                    int max_b, int max_p, int reps, int passes, rq_stream stream, rq_batch_tiles* best,
+                    double* best_ms) {
+  if (!valid(h)) return RQ_EHANDLE;
+  if (reps < 1) return -10;
+  if (passes < 0) return -11;
+  // validates arguments 2-9, sizes the workspace and warms up
+  int rc = rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, stream);
+  if (rc != RQ_OK) return rc;
+  const rq_batch_tiles old{h->tile_m, h->tile_n};
+  rq_batch_tiles chosen = old;
+  double ms = 0.0;
+  if (count > 0) {
+    TuneCtx c{h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, reps, stream, nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&c.e0);
+    if (e == cudaSuccess) {
+      e = cudaEventCreate(&c.e1);
+      if (e != cudaSuccess) cudaEventDestroy(c.e0);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "rq_tune_batched: event");
+    rc = rq_tiles_search(tune_measure, &c, &old, passes, &chosen, &ms);
+    cudaEventDestroy(c.e0);
+    cudaEventDestroy(c.e1);
+    if (rc != RQ_OK) {
+      h->tile_m = old.skinny_m;
+      h->tile_n = old.skinny_n;
+      return rc;
+    }
+  }
+  h->tile_m = chosen.skinny_m;
+  h->tile_n = chosen.skinny_n;
+  if (best) *best = chosen;
+  if (best_ms) *best_ms = ms;
   return RQ_OK;
 }
 

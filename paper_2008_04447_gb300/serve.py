@@ -67,7 +67,10 @@ class Server:
     """Admission + continuous batching over ``lanes`` concurrent GPU launches."""
 
     def __init__(self, budget_bytes=120e9, lanes=3, max_batch=4096, large_mn=2048 * 1024, prec=RQ_MIXED,
-                 device=None):
+                 device=None, tiles=None):
+        """tiles: the batched kernel's tile policy (skinny_m, skinny_n) for every
+        lane, e.g. from Handle.tune_batched on a representative batch; None
+        keeps the library's default."""
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -76,6 +79,9 @@ class Server:
         self.large_mn = large_mn
         self.prec = prec
         self.lanes = [(Handle(), torch.cuda.Stream(device=self.device)) for _ in range(lanes)]
+        if tiles is not None:
+            for h, _ in self.lanes:
+                h.batch_tiles = tuple(tiles)
         self.busy = [None] * lanes       # (requests, event) per lane
         self.pending = []                # submitted, not admitted
         self.ready = []                  # admitted, not launched

@@ -123,3 +123,10 @@ def test_at_most_lanes_launches_in_flight(fakes):
     assert all(r.done >= r.started >= r.admitted >= r.arrival for r in rs)
     st = srv.stats()
     assert st["completed"] == 5
+
+
+def test_tile_policy_reaches_every_lane(fakes):
+    srv = serve.Server(budget_bytes=1e9, lanes=3, device="cpu", tiles=(64, 16))
+    assert all(h.batch_tiles == (64, 16) for h, _ in srv.lanes)
+    srv = serve.Server(budget_bytes=1e9, lanes=2, device="cpu")
+    assert all(not hasattr(h, "batch_tiles") for h, _ in srv.lanes)
