@@ -44,6 +44,22 @@ class RQError(RuntimeError):
     pass
 
 
+def _used_on(t, stream):
+    """Record that device tensor t is used by `stream` (a torch stream or a raw
+    cudaStream_t), unless that is torch's current stream, on which t was
+    allocated: its memory then is not reused before the stream's work is done."""
+    import torch
+    if stream is None:
+        return
+    if isinstance(stream, int):
+        if stream == torch.cuda.current_stream().cuda_stream:
+            return
+        stream = torch.cuda.ExternalStream(stream)
+    elif stream.cuda_stream == torch.cuda.current_stream().cuda_stream:
+        return
+    t.record_stream(stream)
+
+
 class Handle:
     """Owns one rq_handle (workspace cache) on the current CUDA device."""
 
@@ -146,7 +162,11 @@ class Handle:
         outputs, info, d, bounds = self._batch(problems, outputs, svd)
         rc = rq_tuxv_batched(self.h, prec, len(problems), d, *bounds, stream)
         self._check(rc, "rq_tuxv_batched")
-        self._keep = d  # the descriptors must outlive the asynchronous launch
+        # the descriptors must outlive the asynchronous launch: hold the latest
+        # and, when the launch is on another stream than the one they were
+        # allocated on, tell the caching allocator that stream uses them
+        self._keep = d
+        _used_on(d, stream)
         return outputs, info
 
     def tune_batched(self, problems, prec=RQ_MIXED, reps=2, passes=2, stream=None, outputs=None, svd=False):
