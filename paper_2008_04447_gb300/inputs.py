@@ -135,7 +135,10 @@ def graded_torch(m: int, n: int, decades: float, seed: int, device="cuda"):
     return (u * s) @ v.T
 
 
-def lowrank_plus_noise_torch(m: int, n: int, r: int, noise: float, seed: int, device="cuda"):
+def lowrank_plus_noise_parts_torch(m: int, n: int, r: int, noise: float, seed: int, device="cuda"):
+    """The parts of ``lowrank_plus_noise_torch``: Haar U (m x r), sigma_i = i^-2,
+    Haar V (n x r) and the noise matrix (None when noise is 0), drawn in the
+    same order from the same generator."""
     torch = _torch()
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -143,7 +146,13 @@ def lowrank_plus_noise_torch(m: int, n: int, r: int, noise: float, seed: int, de
     s = torch.arange(1, r + 1, device=device, dtype=torch.float64) ** -2.0
     u = haar_torch(m, r, g, device)
     v = haar_torch(n, r, g, device)
+    nz = noise * torch.randn((m, n), generator=g, device=device, dtype=torch.float64) if noise else None
+    return u, s, v, nz
+
+
+def lowrank_plus_noise_torch(m: int, n: int, r: int, noise: float, seed: int, device="cuda"):
+    u, s, v, nz = lowrank_plus_noise_parts_torch(m, n, r, noise, seed, device)
     a = (u * s) @ v.T
-    if noise:
-        a += noise * torch.randn((m, n), generator=g, device=device, dtype=torch.float64)
+    if nz is not None:
+        a += nz
     return a

@@ -1,0 +1,153 @@
+"""GPU parity at the benchmark's full sizes, in the launch configurations
+bench.py times, by properties that hold at any size and by sampled outputs
+the oracle can compute.
+
+* FP64 RQRCP of the 16384 x 16384 graded matrix (b = 64, p = 8);
+* mixed-precision TUXV of the 32768 x 16384 low-rank-plus-noise matrix at
+  k = 512 (b = 64, p = 8);
+* the batched TUXV of the 4096-problem mix (mixed precision, one launch).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2008_04447_gb300 import inputs as I
+
+from gpu_util import build_and_handle, column_norm_mismatch, first_near_tie
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    return build_and_handle()
+
+
+def test_rqrcp_fp64_16384_invariants(H):
+    """jpvt is a permutation; every column of R has the norm of the pivoted
+    column of A (Q is orthogonal; rounding grows like sqrt(m) eps, bound 1e-11
+    relative); and the first block's pivots are the oracle's sample QRCP of the
+    same sketch Omega A (formed here in FP64 by cuBLAS) up to the first decision
+    with a relative gap below 1e-6 (the FP64 near-tie threshold)."""
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    n, b, p = 16384, 64, 8
+    A0 = colmajor(I.graded_torch(n, n, 12, seed=0))
+    Om = colmajor(I.omega_torch(b + p, n, seed=1000))
+    A = torch.empty_like(A0)
+    A.copy_(A0)
+    tau, jpvt, info = H.rqrcp(A, Om, b, p)
+    torch.cuda.synchronize()
+    jp = jpvt.cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.sort(jp), np.arange(n))
+    assert int(info.cpu()[0]) == 0
+    rn = torch.linalg.vector_norm(torch.triu(A), dim=0).cpu().numpy()
+    an = torch.linalg.vector_norm(A0, dim=0)[jpvt.long()].cpu().numpy()
+    assert column_norm_mismatch(rn, an) <= 1e-11
+    B = (Om @ A0).cpu().numpy()
+    sq = O.sample_qrcp(B, b)
+    tie = first_near_tie([sq.gaps], b, 1e-6)
+    upto = b if tie is None else tie
+    assert np.array_equal(jp[:upto], sq.perm[:upto])
+
+
+def test_tuxv_mixed_32768x16384_k512(H):
+    """sigma_i = i^-2 (i <= 2048) with Haar factors plus 1e-6 N(0, 1) noise.
+
+    - info 0; U and V orthonormal (largest entry of U^T U - I, V^T V - I at
+      most 1e-4: FP32 Householder at height 32768); X upper triangular;
+    - ||A - U X V^T||^2 = ||A||^2 - ||X||^2 (X = U^T A V, so U X V^T = A V V^T
+      is a projection) within 1e-4 ||A||^2, the FP32 orthonormality level;
+    - the rank-k error at most 1.05x that of the exact rank-k truncation of
+      the low-rank part (an upper bound of the optimal rank-k error; about the
+      noise floor here), all in FP64 against the FP64 input;
+    - the first block's pivots (TRQRCP on the same inputs: the same sketch and
+      sample kernels) equal the oracle's sample QRCP of the sketch of the
+      bfloat16-rounded Omega and A (formed in FP64 here) up to the first
+      near-tie.  The FP32 sample carries absolute errors of about its largest
+      column norm times FP32 rounding, so decision i is a near-tie when its
+      relative gap is below 1e-4 max_j ||B(:, j)|| / |S_ii| (S_ii: the chosen
+      column's remaining norm; the spectrum falls by 4096x over the block)."""
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED, colmajor
+    m, n, k, b, p = 32768, 16384, 512, 64, 8
+    u, s, v, nz = I.lowrank_plus_noise_parts_torch(m, n, 2048, 1e-6, seed=7)
+    A64 = (u * s) @ v.T
+    A64 += nz
+    del nz
+    A = colmajor(A64.float())
+    Om = colmajor(I.omega_torch(b + p, m, seed=8, dtype=torch.float32))
+    U, X, V, _, info = H.tuxv(A, Om, b, p, k, prec=RQ_MIXED)
+    torch.cuda.synchronize()
+    assert int(info.cpu()[0]) == 0
+    Ud, Xd, Vd = U.double(), X.double(), V.double()
+    eye = torch.eye(k, dtype=torch.float64, device="cuda")
+    assert float((Ud.T @ Ud - eye).abs().max()) <= 1e-4
+    assert float((Vd.T @ Vd - eye).abs().max()) <= 1e-4
+    assert torch.equal(X, torch.triu(X))
+    na2 = float((A64 * A64).sum())
+    R = A64 - Ud @ (Xd @ Vd.T)
+    e2 = float((R * R).sum())
+    del R
+    assert abs(e2 - (na2 - float((Xd * Xd).sum()))) <= 1e-4 * na2
+    T = A64 - (u[:, :k] * s[:k]) @ v[:, :k].T
+    e_ref2 = float((T * T).sum())
+    del T
+    assert e2 ** 0.5 <= 1.05 * e_ref2 ** 0.5, (e2 ** 0.5 / na2 ** 0.5, e_ref2 ** 0.5 / na2 ** 0.5)
+    Y, tau, Rk, jpvt, info2 = H.trqrcp(A, Om, b, p, k, prec=RQ_MIXED)
+    torch.cuda.synchronize()
+    assert int(info2.cpu()[0]) == 0
+    B = (Om.bfloat16().double() @ A.bfloat16().double()).cpu().numpy()
+    sq = O.sample_qrcp(B, b)
+    remaining = np.maximum(np.abs(np.diag(sq.S[:b, :b])), np.finfo(float).tiny)
+    thr = 1e-4 * np.max(np.linalg.norm(B, axis=0)) / remaining
+    near = np.nonzero(np.asarray(sq.gaps[:b]) < thr)[0]
+    upto = b if near.size == 0 else int(near[0])
+    assert upto >= 1, upto       # the first decision is compared (its threshold is 1e-4)
+    jp = jpvt.cpu().numpy().astype(np.int64)
+    assert np.array_equal(jp[:upto], sq.perm[:upto])
+
+
+def test_batched_4096_problem_mix(H):
+    """The batch recipe (seed 0) largest first, as the benchmark launches it:
+    every problem's info 0, U and V orthonormal (largest entry of U^T U - I at
+    most 1e-4: FP32 Householder at heights up to 2048), X upper triangular;
+    on a sample of 24 problems of at most 600 x 400, each one with no
+    near-tie decision (relative gap below 1e-4, scaled per block by the first
+    sample's norm over the block's, as the FP32 sample's rounding grows) has a
+    rank-k error within 1.05x the oracle's with the same bfloat16-rounded
+    sketch inputs."""
+    import torch
+    import bench
+    from paper_2008_04447_gb300 import RQ_MIXED
+    host = bench.batch_inputs(4096, seed=0)
+    dev = bench.to_device_f32(host)
+    order = sorted(range(len(dev)), key=lambda i: -(dev[i][0].shape[0] * dev[i][0].shape[1] * dev[i][4]))
+    probs = [dev[i] for i in order]
+    outs, info = H.tuxv_batched(probs, prec=RQ_MIXED)
+    torch.cuda.synchronize()
+    assert int((info != 0).sum()) == 0
+    worst, below = [], []
+    for (A, Om, b, p, k), (U, X, V) in zip(probs, outs):
+        eye = torch.eye(k, dtype=torch.float64, device="cuda")
+        Ud, Vd = U.double(), V.double()
+        worst.append(torch.maximum((Ud.T @ Ud - eye).abs().max(), (Vd.T @ Vd - eye).abs().max()))
+        below.append((X - torch.triu(X)).abs().max())
+    assert float(torch.stack(worst).max()) <= 1e-4
+    assert float(torch.stack(below).max()) == 0.0
+    g = np.random.default_rng(0)
+    small = [j for j in range(len(probs)) if probs[j][0].shape[0] * probs[j][0].shape[1] <= 600 * 400]
+    checked = 0
+    for j in g.choice(small, size=min(24, len(small)), replace=False):
+        a, om, b, p, k = host[order[j]]
+        a32 = a.astype(np.float32).astype(np.float64)
+        o32 = om.astype(np.float32).astype(np.float64)
+        ref = O.tuxv(a32, o32, b, k, sketch_inputs="bf16")
+        if first_near_tie(ref.tr.gaps, b, 1e-4, ref.tr.sample_norms) is not None:
+            continue
+        U, X, V = (t.cpu().double().numpy() for t in outs[j])
+        e_gpu = np.linalg.norm(a - U @ X @ V.T)
+        e_ref = np.linalg.norm(a - ref.U @ ref.X @ ref.V.T)
+        assert e_gpu <= 1.05 * e_ref, (j, a.shape, k, e_gpu / e_ref)
+        checked += 1
+    assert checked >= 6
