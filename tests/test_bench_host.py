@@ -1,0 +1,25 @@
+"""Host helpers of bench.py (no GPU): the roofline's HBM peak comes from the
+measured peaks file when it is present and from the stated fallback when not;
+the FP64 peak is the derived FP64-pipe figure; the QR flop count reduces to
+4/3 n^3 for a square matrix."""
+import json
+import os
+
+import bench
+
+
+def test_hbm_peak_from_file_and_fallback(tmp_path, monkeypatch):
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 1234.5}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peak, src = bench.hbm_peak_gbs()
+    assert peak == 1234.5 and "MEASURED_PEAKS.json" in src
+    os.remove(tmp_path / "MEASURED_PEAKS.json")
+    peak, src = bench.hbm_peak_gbs()
+    assert peak == 6800.0 and src.startswith("fallback")
+
+
+def test_fp64_peak_and_qr_flops():
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
+    n = 16384
+    assert abs(bench.flops_qr(n, n) / (4.0 * n ** 3 / 3.0) - 1.0) < 1e-14
+    assert abs(bench.flops_qr(300, 200) / (2.0 * 300 * 200 ** 2 - 2.0 * 200 ** 3 / 3.0) - 1.0) < 1e-14
