@@ -124,7 +124,8 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  *   jpvt   n int32 (out): 0-based column permutation, A_in[:, jpvt] = Q R.
  *   info   device int32 (out): 0, or j > 0 when R(j-1, j-1) is exactly zero
  *          (first such j; the factorisation still completes).
- * Precisions: RQ_FP64 and RQ_FP32.
+ * Precisions: RQ_FP64 and RQ_FP32 (RQ_MIXED returns RQ_ENOTIMPL: the BF16
+ * sketch serves the truncated paths).
  */
 int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
              const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
@@ -210,7 +211,8 @@ int rq_padding(double tau, double delta, int* p);
  * reflector kernels as rq_rqrcp but no sampling or pivoting: the QR the paper
  * compares RQRCP against, which is RQRCP with the sampling and pivoting
  * steps removed (Sec. 5.2, Table 3).  A is overwritten as in
- * rq_rqrcp with k = min(m, n); tau has min(m, n) entries.
+ * rq_rqrcp with k = min(m, n); tau has min(m, n) entries.  Precisions and
+ * errors as rq_rqrcp (argument indices follow this signature).
  */
 int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* tau, int* info,
           rq_stream stream);
