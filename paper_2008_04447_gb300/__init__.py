@@ -169,16 +169,34 @@ class Handle:
         _used_on(d, stream)
         return outputs, info
 
-    def tune_batched(self, problems, prec=RQ_MIXED, reps=2, passes=2, stream=None, outputs=None, svd=False):
+    def tune_batched(self, problems, prec=RQ_MIXED, reps=2, passes=2, stream=None, outputs=None, svd=False,
+                     cache=None, key=None):
         """Autotunes the batched kernel's tile policy on these problems (synchronous).
 
         Returns ((skinny_m, skinny_n), ms, outputs, info): the policy now held by
         the handle, the batch's time under it, and the batch's result (the same
-        bits under every policy).
+        bits under every policy).  With cache (a JSON file), a policy stored
+        under the batch's key (``tuning.batch_key`` unless key is given) is
+        taken without timing and the batch simply runs; a newly tuned policy
+        is stored there.
         """
+        from . import tuning
+        if cache is not None:
+            if key is None:
+                import torch
+                dev = problems[0][0].device
+                props = torch.cuda.get_device_properties(dev)
+                key = tuning.batch_key(problems, prec, props.name, props.multi_processor_count)
+            hit = tuning.lookup(cache, key)
+            if hit is not None:
+                self.batch_tiles = hit["tiles"]
+                outputs, info = self.tuxv_batched(problems, prec=prec, stream=stream, outputs=outputs, svd=svd)
+                return tuple(hit["tiles"]), hit["ms"], outputs, info
         outputs, info, d, bounds = self._batch(problems, outputs, svd)
         rc, tiles, ms = _lib.rq_tune_batched(self.h, prec, len(problems), d, *bounds, reps, passes, stream)
         self._check(rc, "rq_tune_batched")
+        if cache is not None:
+            tuning.store(cache, key, tiles, ms)
         return tiles, ms, outputs, info
 
     @property

@@ -4,7 +4,9 @@ rq_tiles_search is driven by synthetic cost functions through its callback:
 it must find the minimum of a separable landscape from any start, measure
 each policy once, stay put when no candidate beats the incumbent by the 1 %
 margin, stop after `passes`, and pass errors and bad times back as statuses.
-The policy calls reject a missing handle before touching the device.
+The policy calls reject a missing handle before touching the device.  The
+JSON cache of tuned policies keys a batch by its class, survives unreadable
+files, and lets Handle.tune_batched skip the timing on a hit.
 """
 import ctypes
 
@@ -114,3 +116,55 @@ def test_argument_checks(lib):
     assert _lib.rq_set_batch_tiles(None, 32, 32) == _lib.RQ_EHANDLE
     assert _lib.rq_get_batch_tiles(None)[0] == _lib.RQ_EHANDLE
     assert lib.rq_tune_batched(None, 2, 0, None, 1, 1, 1, 1, 0, 1, 1, None, None, None) == _lib.RQ_EHANDLE
+
+
+def test_batch_key_names_the_class_of_a_batch():
+    import torch
+    from paper_2008_04447_gb300 import tuning
+    probs = [(torch.zeros(300, 200), None, 16, 8, 40), (torch.zeros(64, 64), None, 8, 8, 8)]
+    k1 = tuning.batch_key(probs, 2, "GB300", 152)
+    assert k1 == "GB300/sm152/prec2/count2/m512/n256/k64"
+    assert tuning.batch_key([(torch.zeros(257, 129), None, 16, 8, 33)] * 2, 2, "GB300", 152) == k1
+    assert tuning.batch_key(probs, 1, "GB300", 152) != k1
+    assert tuning.batch_key(probs * 2, 2, "GB300", 152) != k1
+    assert tuning.batch_key(probs, 2, "GB300", 148) != k1
+
+
+def test_cache_round_trip_and_unreadable_files(tmp_path):
+    import json
+    import os
+    from paper_2008_04447_gb300 import tuning
+    path = str(tmp_path / "tiles.json")
+    assert tuning.lookup(path, "k") is None
+    tuning.store(path, "k", (64, 16), 1.5)
+    assert tuning.lookup(path, "k") == {"tiles": [64, 16], "ms": 1.5}
+    tuning.store(path, "k2", (0, 256), None)
+    assert tuning.lookup(path, "k")["tiles"] == [64, 16] and tuning.lookup(path, "k2")["ms"] is None
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert tuning.lookup(path, "k") is None
+    tuning.store(path, "k", (32, 32), 2.0)          # an unreadable file is replaced
+    assert tuning.lookup(path, "k")["tiles"] == [32, 32]
+    with open(path, "w") as f:
+        json.dump({"k": {"tiles": [-1, 3]}, "j": [1, 2]}, f)
+    assert tuning.lookup(path, "k") is None and tuning.lookup(path, "j") is None
+    assert not [f for f in os.listdir(tmp_path) if f.startswith(".tiles")]   # no temporary left behind
+
+
+def test_tune_batched_fills_then_uses_the_cache(tmp_path, monkeypatch):
+    import paper_2008_04447_gb300 as P
+    calls = []
+    h = object.__new__(P.Handle)
+    h.h = None
+    monkeypatch.setattr(P.Handle, "_batch", staticmethod(lambda problems, outputs, svd: ("outs", "info", "d",
+                                                                                        (1, 1, 1, 1, 0))))
+    monkeypatch.setattr(P._lib, "rq_tune_batched", lambda *a: (calls.append("tune"), (0, (64, 16), 1.25))[1])
+    monkeypatch.setattr(P._lib, "rq_set_batch_tiles", lambda hh, m, n: (calls.append(("set", m, n)), 0)[1])
+    monkeypatch.setattr(P, "rq_tuxv_batched", lambda *a: (calls.append("run"), 0)[1])
+    cache = str(tmp_path / "tiles.json")
+    assert h.tune_batched([("A",)], cache=cache, key="K") == ((64, 16), 1.25, "outs", "info")
+    assert calls == ["tune"]
+    calls.clear()
+    tiles, ms, outs, info = h.tune_batched([("A",)], cache=cache, key="K")
+    assert (tiles, ms, outs, info) == ((64, 16), 1.25, "outs", "info")
+    assert calls == [("set", 64, 16), "run"]                      # no timing on a hit
