@@ -8,7 +8,9 @@ large ones to the whole-GPU ``rq_tuxv``.  Up to ``lanes`` launches are on the
 GPU at once, each on its own CUDA stream with its own library handle, so
 requests that arrive while others run start as soon as a lane and memory free
 up, and their work overlaps on the device.  A request's result does not
-depend on what it was batched with (each problem is computed by one CTA).
+depend on what it was batched with (each problem is computed by one CTA).  A
+launch the library refuses fails the requests of that launch (``wait`` raises)
+and frees their memory; the server goes on with the others.
 
 Only argument marshalling and scheduling live here; all arithmetic runs in the
 CUDA library.
@@ -47,6 +49,7 @@ class Request:
     info: object = None
     nbytes: int = 0
     large: bool = False
+    error: object = None             # the exception that failed the request's launch, if any
     _ev: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -56,6 +59,8 @@ class Request:
     def wait(self, timeout=None):
         if not self._ev.wait(timeout):
             raise TimeoutError("request not finished")
+        if self.error is not None:
+            raise RuntimeError("request failed") from self.error
         return self.out
 
     @property
@@ -87,6 +92,7 @@ class Server:
         self.ready = []                  # admitted, not launched
         self.used = 0
         self.completed = []
+        self.failed = []
         self.rejected = 0
         self.lock = threading.Lock()
         self._stop = False
@@ -141,24 +147,35 @@ class Server:
                 ids = {id(r) for r in batch}
                 self.ready = [r for r in self.ready if id(r) not in ids]
                 batch.sort(key=lambda r: -(r.A.shape[0] * r.A.shape[1] * r.k))
-            with torch.cuda.stream(st):
-                for r in batch:
-                    r.started = now
-                if batch[0].large:
-                    r = batch[0]
-                    U, X, V = r.out
-                    prec = RQ_MIXED if self.prec == RQ_MIXED else RQ_FP32
-                    U2, X2, V2, _, info = h.tuxv(r.A, r.Omega, r.b, r.p, r.k, prec=prec, stream=st)
-                    r.out = (U2, X2, V2)
-                    r.info = info
-                else:
-                    outs, info = h.tuxv_batched([(r.A, r.Omega, r.b, r.p, r.k) for r in batch], prec=self.prec,
-                                                stream=st, outputs=[r.out for r in batch])
-                    for j, r in enumerate(batch):
-                        r.info = info[j:j + 1]
-                ev = torch.cuda.Event()
-                ev.record(st)
+            for r in batch:
+                r.started = now
+            try:
+                with torch.cuda.stream(st):
+                    if batch[0].large:
+                        r = batch[0]
+                        prec = RQ_MIXED if self.prec == RQ_MIXED else RQ_FP32
+                        U2, X2, V2, _, info = h.tuxv(r.A, r.Omega, r.b, r.p, r.k, prec=prec, stream=st)
+                        r.out = (U2, X2, V2)
+                        r.info = info
+                    else:
+                        outs, info = h.tuxv_batched([(r.A, r.Omega, r.b, r.p, r.k) for r in batch],
+                                                    prec=self.prec, stream=st, outputs=[r.out for r in batch])
+                        for j, r in enumerate(batch):
+                            r.info = info[j:j + 1]
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+            except Exception as exc:  # the library refused the launch: fail these requests, keep serving
+                self._fail(batch, exc, now)
+                continue
             self.busy[i] = (batch, ev)
+
+    def _fail(self, batch, exc, now):
+        for r in batch:
+            r.error = exc
+            r.done = now
+            self.used -= r.nbytes
+            self.failed.append(r)
+            r._ev.set()
 
     def pump(self):
         """One scheduling pass: retire finished launches, admit, launch."""
@@ -205,4 +222,4 @@ class Server:
             span = float("nan")
         return {"completed": len(self.completed), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "req_per_s": len(self.completed) / span,
-                "rejected": self.rejected}
+                "rejected": self.rejected, "failed": len(self.failed)}

@@ -1,6 +1,7 @@
 """Host logic of the continuous-batching server (no GPU): admission against the
 HBM budget, routing of large and small requests, at most `lanes` launches in
-flight, completion and draining.  The library handle, CUDA streams and events
+flight, completion and draining; a launch the library refuses (an injected
+error) fails its own requests only, and waits time out on the host.  The library handle, CUDA streams and events
 are replaced by fakes that record the calls; a fake event completes when the
 test says so."""
 import contextlib
@@ -130,3 +131,44 @@ def test_tile_policy_reaches_every_lane(fakes):
     assert all(h.batch_tiles == (64, 16) for h, _ in srv.lanes)
     srv = serve.Server(budget_bytes=1e9, lanes=2, device="cpu")
     assert all(not hasattr(h, "batch_tiles") for h, _ in srv.lanes)
+
+
+class FailingHandle(FakeHandle):
+    """Refuses any batch holding a problem with 77 rows (an injected library error)."""
+
+    def tuxv_batched(self, problems, prec=None, stream=None, outputs=None):
+        if any(t[0].shape[0] == 77 for t in problems):
+            FakeHandle.log.append(("refused", len(problems)))
+            raise RuntimeError("rq_tuxv_batched failed with status -1001")
+        return super().tuxv_batched(problems, prec, stream, outputs)
+
+
+def test_a_failed_launch_fails_its_requests_and_serving_goes_on(fakes, monkeypatch):
+    monkeypatch.setattr(serve, "Handle", FailingHandle)
+    srv = serve.Server(budget_bytes=1e12, lanes=1, device="cpu")
+    bad = [srv.submit(*req(77, 40)), srv.submit(*req(60, 40))]       # batched together, refused together
+    srv.pump()
+    assert all(r.error is not None for r in bad) and srv.used == 0 and srv.busy == [None]
+    for r in bad:
+        with pytest.raises(RuntimeError, match="request failed"):
+            r.wait(0)
+    good = srv.submit(*req(64, 48))
+    srv.pump()
+    finish_all()
+    srv.pump()
+    assert good.wait(0) is not None and good.error is None
+    st = srv.stats()
+    assert st["failed"] == 2 and st["completed"] == 1 and srv.used == 0
+
+
+def test_waits_time_out_on_the_host(fakes):
+    srv = serve.Server(budget_bytes=1e12, lanes=1, device="cpu")
+    r = srv.submit(*req(64, 48))
+    srv.pump()                                    # launched; its event never completes
+    with pytest.raises(TimeoutError):
+        r.wait(0.01)
+    with pytest.raises(TimeoutError):
+        srv.drain(timeout=0.05)
+    finish_all()
+    srv.drain(timeout=1.0)
+    assert r.wait(0) is not None
