@@ -172,3 +172,22 @@ def test_waits_time_out_on_the_host(fakes):
     finish_all()
     srv.drain(timeout=1.0)
     assert r.wait(0) is not None
+
+
+def test_an_allocation_failure_at_admission_fails_that_request(fakes, monkeypatch):
+    srv = serve.Server(budget_bytes=1e12, lanes=1, device="cpu")
+    real = torch.empty
+
+    def empty(shape, **kw):
+        if shape[1] == 99:
+            raise RuntimeError("CUDA out of memory")
+        return real(shape, **kw)
+    monkeypatch.setattr(torch, "empty", empty)
+    bad = srv.submit(*req(99, 40))
+    good = srv.submit(*req(64, 40))
+    srv.pump()
+    with pytest.raises(RuntimeError, match="request failed"):
+        bad.wait(0)
+    finish_all()
+    srv.pump()
+    assert good.wait(0) is not None and srv.used == 0 and srv.stats()["failed"] == 1
