@@ -180,8 +180,9 @@ __device__ void panel_b(float* P, int ldp, int mt, int bj, float* Yout, int ldy,
   for (int j = 0; j < bj; ++j) {
     float* aj = P + (size_t)j * ldp;
     // squared norm below row j: float-float per thread and warp (FP64 for a
-    // warp holding an entry outside [2^-60, 2^55]; about 2^-44 relative for
-    // entries of at least 2^-38, toward FP32's accuracy below that), combined
+    // warp holding an entry outside [2^-60, 2^55]; about 2^-46 relative while
+    // the column's largest entries are at least 2^-52, falling toward 2^-34
+    // for a column of entries near 2^-60), combined
     // in FP64 by thread 0, which forms the reflector's scalars (FP64 is slow
     // on this part, so it stays off the all-thread path)
     {
@@ -302,8 +303,8 @@ __device__ void sample_qrcp_b(float* B, int l, int nt, int steps, int* jp, doubl
   const double tol = 3.4526698300124393e-04;  // sqrt(FLT_EPSILON): the sample is held in FP32
   for (int c = tid; c < nt; c += NT) {
     // squared column norm in float-float arithmetic (FP64 when an entry lies
-    // outside [2^-60, 2^55]; about 2^-44 relative for entries of at least
-    // 2^-38, toward FP32's accuracy below that)
+    // outside [2^-60, 2^55]; about 2^-46 relative while the column's largest
+    // entries are at least 2^-52, falling toward 2^-34 near 2^-60)
     const float* bc = B + (size_t)c * l;
     float h = 0.f, lo = 0.f;
     bool oor = false;

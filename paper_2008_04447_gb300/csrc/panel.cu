@@ -379,10 +379,10 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
     double x2d = 0.0;
     if constexpr (kF32) {
       // float-float squares while every |a_j(g)| of the warp lies in
-      // [2^-60, 2^55] (no overflow for up to 2^17 rows; about 2^-44 relative
-      // for entries of at least 2^-38, falling toward FP32's accuracy below
-      // that, where the low parts become subnormal); otherwise this warp sums
-      // in FP64
+      // [2^-60, 2^55] (no overflow for up to 2^17 rows; about 2^-46 relative
+      // while the column's largest entries are at least 2^-52, falling toward
+      // 2^-34 for a column of entries near 2^-60, where the squares' low parts
+      // become subnormal); otherwise this warp sums in FP64
       const float fa = fabsf(aj);
       const bool out_of_range = mine && aj != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
       if (__any_sync(0xffffffffu, out_of_range)) {

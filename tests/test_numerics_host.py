@@ -9,7 +9,9 @@ methods; the GPU parity tests cover the kernels that use them):
   results (Markstein's method): at least 44 correct bits;
 * float-float (TwoSum) sums of squares of FP32 data, summed per thread and
   then by a 32-lane tree as the kernels do: relative error at most 2^-44 for
-  entries of at least 2^-38, checked against an exact sum.
+  entries of at least 2^-52 (measured about 2^-46 to 2^-48), checked against
+  an exact sum; a column of entries near 2^-58, where the squares' low parts
+  are subnormal, still within 2^-30.
 """
 import math
 
@@ -96,16 +98,18 @@ def ff_thread_then_tree(x, per):
 def test_float_float_sums_of_squares_are_fp64_accurate():
     """In the kernels' shape (a few rows per thread, or up to 128 for a sample
     column, then a 32-lane tree) the float-float sum of squares of FP32 entries
-    of magnitude at least 2^-38 is accurate to about 2^-44; below that the low
-    parts become subnormal and the accuracy falls toward FP32's."""
+    of magnitude at least 2^-52 is accurate to 2^-44.  A square's rounding
+    error a^2 2^-24 stays a normal float down to a = 2^-51; below, the low
+    parts lose bits, and at the kernels' lower range limit (2^-60, where they
+    switch to FP64) a column of such entries is accurate to about 2^-34."""
     rng = np.random.default_rng(2)
     for per in (1, 8, 128):
-        for scale in (1e-9, 1e-3, 1.0, 1e6, 1e15):
+        for scale in (2.0 ** -45, 1e-9, 1e-3, 1.0, 1e6, 1e15):
             x = (rng.standard_normal(32 * per) * scale * np.exp(rng.uniform(-3, 3, 32 * per))).astype(np.float32)
-            x = np.where(np.abs(x) >= 2.0 ** -38, x, F32(2.0 ** -38))
+            x = np.where(np.abs(x) >= 2.0 ** -52, x, F32(2.0 ** -52))
             exact = math.fsum(float(a) * float(a) for a in x)   # products of FP32 values are exact in FP64
             got = ff_thread_then_tree(x, per)
             assert abs(got - exact) <= 2.0 ** -44 * exact, (per, scale, abs(got - exact) / exact)
-    x = (rng.standard_normal(32 * 8) * 1e-15).astype(np.float32)    # entries near 2^-50
+    x = (rng.standard_normal(32 * 8) * 2.0 ** -58).astype(np.float32)    # entries near 2^-58
     exact = math.fsum(float(a) * float(a) for a in x)
-    assert abs(ff_thread_then_tree(x, 8) - exact) <= 2.0 ** -22 * exact
+    assert abs(ff_thread_then_tree(x, 8) - exact) <= 2.0 ** -30 * exact
