@@ -409,14 +409,15 @@ def leg_tuxv(h, steps=3, warmup=3, shape=(32768, 16384, 512)):
     return out
 
 
-def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24, tune=True):
+def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True):
     """4096 uneven problems in one persistent launch (mixed precision).
 
     With tune, the tile policy is autotuned on the batch first (outside the
-    timed region; every policy gives the same bits)."""
+    timed region; every policy gives the same bits).  Quality: on a sample of
+    problems, the rank-k error over the optimal rank-k error of the FP64 input
+    (numpy's SVD); the comparison with the oracle is the GPU tests' job."""
     import numpy as np
     import torch
-    import oracle as O
     from paper_2008_04447_gb300 import RQ_MIXED
     order = sorted(range(len(dev)), key=lambda i: -(dev[i][0].shape[0] * dev[i][0].shape[1] * dev[i][4]))
     probs = [dev[i] for i in order]
@@ -442,23 +443,23 @@ def leg_batched(h, host, dev, steps=3, warmup=2, oracle_sample=24, tune=True):
     ms = e0.elapsed_time(e1) / steps
     flops = sum(4.0 * k * A.shape[0] * A.shape[1] + 2.0 * (b + p) * A.shape[0] * A.shape[1] for A, Om, b, p, k in probs)
     byts = sum(4.0 * A.shape[0] * A.shape[1] * (3 + (k + b - 1) // b) for A, Om, b, p, k in probs)
-    # error ratio against the FP64 oracle on a sample of problems
+    # rank-k error over the optimal rank-k error (Eckart-Young) on a sample of problems
     ratios = []
     g = np.random.default_rng(0)
-    for j in g.choice(len(probs), size=min(oracle_sample, len(probs)), replace=False):
+    for j in g.choice(len(probs), size=min(quality_sample, len(probs)), replace=False):
         a, om, b, p, k = host[order[j]]
         if a.shape[0] * a.shape[1] > 600 * 400:
             continue
         U, X, V = (t.cpu().double().numpy() for t in outs[j])
-        ref = O.tuxv(a, om, b, k)
-        e_gpu = np.linalg.norm(a - U @ X @ V.T)
-        e_ref = np.linalg.norm(a - ref.U @ ref.X @ ref.V.T)
-        ratios.append(e_gpu / e_ref)
+        sv = np.linalg.svd(a, compute_uv=False)
+        e_opt = float(np.sqrt(np.sum(sv[k:] ** 2)))
+        if e_opt > 0:
+            ratios.append(float(np.linalg.norm(a - U @ X @ V.T)) / e_opt)
     return {"workload": f"batched_tuxv_mixed_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
             "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
             "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "info_nonzero": int((info != 0).sum()), **tuning,
-            "error_ratio_vs_fp64_oracle": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
-                                           "max": float(np.max(ratios)) if ratios else None}}
+            "error_over_svd_optimum": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
+                                       "max": float(np.max(ratios)) if ratios else None}}
 
 
 def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9,
@@ -557,7 +558,7 @@ def main():
     barrier(ws)
     if args.only_batched or args.only == "batched":
         host = batch_inputs(args.batch, seed=0)
-        print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), oracle_sample=0)}), flush=True)
+        print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), quality_sample=0)}), flush=True)
         return
     if args.only == "serving":
         host = batch_inputs(args.batch, seed=0)
