@@ -2,9 +2,10 @@
 bench.py times, by properties that hold at any size and by sampled outputs
 the oracle can compute.
 
-* FP64 RQRCP of the 16384 x 16384 graded matrix (b = 64, p = 8);
+* FP64 and FP32 RQRCP of the 16384 x 16384 graded matrix (b = 64, p = 8);
 * mixed-precision TUXV of the 32768 x 16384 low-rank-plus-noise matrix at
-  k = 512 (b = 64, p = 8);
+  k = 512 (b = 64, p = 8), and against the oracle on the same recipe scaled
+  to 8192 x 4096 at k = 128 (the oracle's size limit in a test);
 * the batched TUXV of the 4096-problem mix (mixed precision, one launch).
 """
 import numpy as np
@@ -49,6 +50,60 @@ def test_rqrcp_fp64_16384_invariants(H):
     tie = first_near_tie([sq.gaps], b, 1e-6)
     upto = b if tie is None else tie
     assert np.array_equal(jp[:upto], sq.perm[:upto])
+
+
+def test_rqrcp_fp32_16384_invariants(H):
+    """FP32 storage and 3xTF32 updates: the same invariants as the FP64 case
+    with FP32 bounds -- column norms of R equal the pivoted columns' to 2e-4
+    (about 10x sqrt(n) times FP32 rounding) and the first block's pivots equal
+    the oracle's sample QRCP of Omega A (FP64 from the FP32 inputs) up to the
+    first decision with a relative gap below 1e-4 (the spectrum falls by 0.9x
+    over the block, so the FP32 sample's rounding is not amplified)."""
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    n, b, p = 16384, 64, 8
+    A0 = colmajor(I.graded_torch(n, n, 12, seed=0).float())
+    Om = colmajor(I.omega_torch(b + p, n, seed=1000, dtype=torch.float32))
+    A = torch.empty_like(A0)
+    A.copy_(A0)
+    tau, jpvt, info = H.rqrcp(A, Om, b, p)
+    torch.cuda.synchronize()
+    jp = jpvt.cpu().numpy().astype(np.int64)
+    assert np.array_equal(np.sort(jp), np.arange(n))
+    assert int(info.cpu()[0]) == 0
+    rn = torch.linalg.vector_norm(torch.triu(A).double(), dim=0).cpu().numpy()
+    an = torch.linalg.vector_norm(A0.double(), dim=0)[jpvt.long()].cpu().numpy()
+    assert column_norm_mismatch(rn, an) <= 2e-4
+    B = (Om.double() @ A0.double()).cpu().numpy()
+    sq = O.sample_qrcp(B, b)
+    tie = first_near_tie([sq.gaps], b, 1e-4)
+    upto = b if tie is None else tie
+    assert np.array_equal(jp[:upto], sq.perm[:upto])
+
+
+@pytest.mark.parametrize("noise", [1e-6, 1e-10])
+def test_tuxv_mixed_8192x4096_against_the_oracle(H, noise):
+    """The TUXV recipe scaled to 8192 x 4096 (rank 1024 part, sigma_i = i^-2),
+    k = 128, b = 64, p = 8, mixed precision: the rank-k error, in FP64 against
+    the FP64 input, within 1.05x the oracle's with the same bfloat16-rounded
+    sketch inputs.  At noise 1e-6 both sit near the noise floor; at 1e-10 the
+    tail of the spectrum sets the error, so the ratio is a real test."""
+    import torch
+    from paper_2008_04447_gb300 import RQ_MIXED
+    from gpu_util import to_dev
+    m, n, k, b, p = 8192, 4096, 128, 64, 8
+    a = I.lowrank_plus_noise(m, n, 1024, noise, seed=3)
+    om = I.omega(b + p, m, seed=4)
+    a32 = a.astype(np.float32).astype(np.float64)
+    o32 = om.astype(np.float32).astype(np.float64)
+    U, X, V, _, info = H.tuxv(to_dev(a32, torch.float32), to_dev(o32, torch.float32), b, p, k, prec=RQ_MIXED)
+    torch.cuda.synchronize()
+    assert int(info.cpu()[0]) == 0
+    ref = O.tuxv(a32, o32, b, k, sketch_inputs="bf16")
+    U, X, V = (t.cpu().double().numpy() for t in (U, X, V))
+    e_gpu = np.linalg.norm(a - U @ X @ V.T)
+    e_ref = np.linalg.norm(a - ref.U @ ref.X @ ref.V.T)
+    assert e_gpu <= 1.05 * e_ref, (noise, e_gpu / e_ref)
 
 
 def test_tuxv_mixed_32768x16384_k512(H):
