@@ -106,6 +106,12 @@ int rq_profile_enable(rq_handle h, int enable);
 int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double* bytes,
                     long long* launches);
 
+/* Largest block size b and sample rank l = b + p of the single-problem
+ * calls (one panel and one sample QRCP launch hold them; larger values return
+ * the argument's index). */
+#define RQ_MAX_B 256
+#define RQ_MAX_L 384
+
 /*
  * rq_rqrcp -- Randomized QR with column pivoting, Alg. 4 (Sec. 3.4), with the
  * sample update formula Eq. (update1).
@@ -115,8 +121,8 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  *          below the diagonal of columns 0..k-1 the Householder vectors v
  *          (v_1 = 1 implicit, H = I - v tau v^T); the block A[k:m, k:n] holds
  *          the trailing matrix (R22) left by the last block update.
- *   b      block size (pivots per sample), 1 <= b.
- *   p      oversampling; the sample has l = b + p rows, p >= 0.
+ *   b      block size (pivots per sample), 1 <= b <= RQ_MAX_B.
+ *   p      oversampling; the sample has l = b + p rows, p >= 0, l <= RQ_MAX_L.
  *   k      factorisation rank, 1 <= k <= min(m, n).
  *   Omega  l x m Gaussian compression matrix (ldo >= l), read only; the same
  *          Omega serves every block through the update formula.

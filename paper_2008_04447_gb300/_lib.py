@@ -24,6 +24,7 @@ RQ_ENOTIMPL = -1003
 RQ_EHANDLE = -1004
 RQ_ETOOBIG = -1005
 RQ_NOALLOC_SCRATCH_BYTES = 16 << 20
+RQ_MAX_B, RQ_MAX_L = 256, 384
 
 RQ_FP64, RQ_FP32, RQ_MIXED = 0, 1, 2
 RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR, RQ_OP_RSRQRCP = 0, 1, 2, 3, 4

@@ -25,6 +25,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxB = 256;
+static_assert(RQ_MAX_B <= kMaxB, "the panel kernels hold the largest block");
 constexpr int kMaxRec = 20;  // partial records summed per thread: G <= kMaxRec * kWarps = 160
 
 template <typename TS>

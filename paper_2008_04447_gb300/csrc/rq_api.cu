@@ -764,8 +764,8 @@ int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b,
   if (rc) return rc == -2 ? -3 : rc;
   if (m < 1) return -4;
   if (n < 1) return -5;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (!bytes) return -9;
   const int l = (op == RQ_OP_QR) ? 1 : b + p;
   if (op == RQ_OP_RQRCP || op == RQ_OP_QR || op == RQ_OP_RSRQRCP) {
@@ -853,8 +853,8 @@ int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (k < 1 || k > (m < n ? m : n)) return -9;
   if (!Omega) return -10;
   if (ldo < b + p) return -11;
@@ -879,8 +879,8 @@ int rq_rsrqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (k < 1 || k > (m < n ? m : n)) return -9;
   if (!tau) return -11;
   if (!jpvt) return -12;
@@ -902,7 +902,7 @@ int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* ta
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
+  if (b < 1 || b > RQ_MAX_B) return -7;
   if (!tau) return -8;
   if (!info) return -9;
   const int k = m < n ? m : n;
@@ -924,8 +924,8 @@ int rq_trqrcp(rq_handle h, int prec, int m, int n, const void* A, int lda, int b
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (k < 1 || k > (m < n ? m : n)) return -9;
   if (!Omega) return -10;
   if (ldo < b + p) return -11;
@@ -956,8 +956,8 @@ int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, 
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (k < 1 || k > (m < n ? m : n)) return -9;
   if (!Omega) return -10;
   if (ldo < b + p) return -11;
@@ -987,8 +987,8 @@ int rq_tuxv_iter(rq_handle h, int prec, int m, int n, const void* A, int lda, in
   if (n < 1) return -4;
   if (!A) return -5;
   if (lda < m) return -6;
-  if (b < 1) return -7;
-  if (p < 0) return -8;
+  if (b < 1 || b > RQ_MAX_B) return -7;
+  if (p < 0 || b + p > RQ_MAX_L) return -8;
   if (k < 1 || k > (m < n ? m : n)) return -9;
   if (jmax < 1) return -10;
   if (!Omega) return -11;

@@ -165,8 +165,8 @@ extern "C" int rq_rqrcp_noalloc(int prec, int m, int n, void* A, int lda, int b,
   if (n < 1) return -3;
   if (!A) return -4;
   if (lda < m) return -5;
-  if (b < 1) return -6;
-  if (p < 0) return -7;
+  if (b < 1 || b > RQ_MAX_B) return -6;
+  if (p < 0 || b + p > RQ_MAX_L) return -7;
   if (k < 1 || k > (m < n ? m : n)) return -8;
   if (!Omega) return -9;
   if (ldo < b + p) return -10;

@@ -33,6 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSteps = 256;
+static_assert(RQ_MAX_B <= kMaxSteps && RQ_MAX_L <= kMaxSteps + 128, "the sample kernel holds the largest sample");
 constexpr int kMaxRecS = 8;  // candidate records per lane: G <= 256
 
 template <typename TS>

@@ -51,3 +51,21 @@ def test_null_handle_is_rejected(lib):
     assert L.rq_destroy(None) == _lib.RQ_EHANDLE
     assert L.rq_rqrcp(None, 0, 1, 1, None, 1, 1, 0, 1, None, 1, None, None, None, None) == _lib.RQ_EHANDLE
     assert L.rq_launch_count(None) == -1
+
+
+def test_header_constants_match_the_binding():
+    from paper_2008_04447_gb300 import _lib
+    txt = open(os.path.join(ROOT, "include", "rqrcp.h")).read()
+    defs = dict(re.findall(r"^#define (RQ_\w+)\s+\(?(-?\d+)", txt, flags=re.M))
+    for name in ("RQ_OK", "RQ_ENOMEM", "RQ_ECUDA", "RQ_ETIMEOUT", "RQ_ENOTIMPL", "RQ_EHANDLE", "RQ_ETOOBIG",
+                 "RQ_FP64", "RQ_FP32", "RQ_MIXED", "RQ_MAX_B", "RQ_MAX_L"):
+        assert int(defs[name]) == getattr(_lib, name), name
+
+
+def test_block_and_sample_limits_are_argument_errors(lib):
+    from paper_2008_04447_gb300 import _lib
+    L = _lib.load()
+    x = 1   # never dereferenced: the argument checks return first
+    assert L.rq_rqrcp_noalloc(0, 300, 300, x, 300, _lib.RQ_MAX_B + 1, 8, 10, x, 300, x, x, x, None) == -6
+    assert L.rq_rqrcp_noalloc(0, 300, 300, x, 300, _lib.RQ_MAX_B, _lib.RQ_MAX_L - _lib.RQ_MAX_B + 1, 10, x, 400,
+                              x, x, x, None) == -7

@@ -137,3 +137,5 @@ def test_bad_arguments_return_negative_index(H):
     assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, 2, 2, 5, A, 4, t, j, i) == -9   # k > min(m, n)
     assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, 2, 2, 4, A, 3, t, j, i) == -11  # ldo < l
     assert _lib.rq_rqrcp(H.h, 7, 4, 4, A, 4, 2, 2, 4, A, 4, t, j, i) == -2   # precision
+    assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, _lib.RQ_MAX_B + 1, 2, 4, A, 4, t, j, i) == -7   # b > RQ_MAX_B
+    assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, 2, _lib.RQ_MAX_L - 1, 4, A, 4, t, j, i) == -8   # b + p > RQ_MAX_L
