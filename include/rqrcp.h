@@ -107,8 +107,12 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
                     long long* launches);
 
 /* Largest block size b and sample rank l = b + p of the single-problem
- * calls (one panel and one sample QRCP launch hold them; larger values return
- * the argument's index). */
+ * calls (larger values return the argument's index).  Blocks of up to 64
+ * columns run on the register-resident panel kernel; larger ones on the
+ * general panel kernel, whose shared-memory tile (b^2 + b ceil(m / SMs)
+ * values) must fit one CTA: about b <= 110 for FP64 at m = 16384.  A panel
+ * that does not fit returns RQ_ENOTIMPL when the factorisation reaches it,
+ * with A partly updated. */
 #define RQ_MAX_B 256
 #define RQ_MAX_L 384
 
