@@ -61,6 +61,7 @@ def parse():
                     help="run only this leg and print its JSON (profiling)")
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched leg")
+    ap.add_argument("--no-tune", action="store_true", help="batched leg: keep the default tile policy (profiling)")
     ap.add_argument("--tuxv-shape", default="32768,16384,512", help="m,n,k of the TUXV leg")
     ap.add_argument("--sweep", default="", help="paper-shaped timing sweeps instead of the bench line (comma list of "
                     + ", ".join(SWEEPS) + ", or 'all'); one JSON line per point")
@@ -558,7 +559,7 @@ def main():
     barrier(ws)
     if args.only_batched or args.only == "batched":
         host = batch_inputs(args.batch, seed=0)
-        print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), quality_sample=0)}), flush=True)
+        print(json.dumps({"batched": leg_batched(Handle(), host, to_device_f32(host), quality_sample=0, tune=not args.no_tune)}), flush=True)
         return
     if args.only == "serving":
         host = batch_inputs(args.batch, seed=0)
@@ -778,7 +779,7 @@ def main():
             host = batch_inputs(args.batch, seed=0)
             dev = to_device_f32(host)
             if "batched" in legs:
-                line["batched"] = leg_batched(h, host, dev)
+                line["batched"] = leg_batched(h, host, dev, tune=not args.no_tune)
             if "serving" in legs:
                 line["serving"] = leg_serving(dev, tiles=line.get("batched", {}).get("tiles"))
             del dev
