@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--decades", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg but the timed RQRCP")
-    ap.add_argument("--legs", default="qr,e2e,fp32,rsrqrcp,cpu,tuxv,batched,serving",
+    ap.add_argument("--legs", default="qr,e2e,fp32,rsrqrcp,cpu,slices,tuxv,batched,serving",
                     help="extra legs to run (comma list); --no-extras clears it")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the timed RQRCP")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
@@ -367,6 +367,37 @@ def leg_e2e_pipelined(h, Ah, Ao_ref, Om, b, p, fl, like, local, steps=3):
            "steps": steps, "matches_serial": bool(torch.equal(Ao, Ao_ref)), "clocks": clk.stop(),
            "overlap": "step i+1's input copy and step i's result copy beside the factorisations"}
     del bufs, keep
+    return out
+
+
+def leg_slices(h):
+    """Exactness of 8-bit slice products on the tensor cores: integer matrices
+    with entries in [-255, 255] (the slices of an exact FP64 split) through
+    rq_gemm_bf16, against the exact integer product.  Every sum stays below
+    2^24 up to K = 256 (also with all entries 255), so those results are exact
+    if the tensor core's FP32 accumulation keeps every bit of them; K = 2048 is
+    past that bound and shows the rounding of FP32 sums that large."""
+    import numpy as np
+    import torch
+    from paper_2008_04447_gb300 import colmajor
+    out = {}
+    g = np.random.default_rng(0)
+    M = N = 128
+    for kind in ("random", "max"):
+        for K in (32, 64, 128, 256, 2048):
+            if kind == "random":
+                a, b = g.integers(-255, 256, (M, K)), g.integers(-255, 256, (K, N))
+            else:
+                a, b = np.full((M, K), 255), np.full((K, N), 255)
+            exact = a.astype(np.int64) @ b.astype(np.int64)
+            A = colmajor(torch.as_tensor(a, dtype=torch.float32)).cuda()
+            B = colmajor(torch.as_tensor(b, dtype=torch.float32)).cuda()
+            C, info = h.gemm_bf16(A, B)
+            torch.cuda.synchronize()
+            err = np.abs(C.cpu().double().numpy() - exact)
+            out[f"{kind}_k{K}"] = {"max_abs_err": float(err.max()), "max_abs": float(np.abs(exact).max()),
+                                   "info": int(info.cpu()[0])}
+    out["exact_below_2^24"] = all(v["max_abs_err"] == 0 for key, v in out.items() if not key.endswith("k2048"))
     return out
 
 
@@ -767,6 +798,11 @@ def main():
             torch.cuda.empty_cache()
     del A0, A
     torch.cuda.empty_cache()
+    if "slices" in legs:
+        try:
+            line["slices"] = leg_slices(h)
+        except Exception as exc:  # a failing extra leg must not lose the headline line
+            line["slices"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     if "tuxv" in legs:
         try:
             line["tuxv"] = leg_tuxv(h)

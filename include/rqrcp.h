@@ -310,6 +310,26 @@ int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems
                     int max_b, int max_p, rq_stream stream);
 
 /*
+ * rq_gemm_bf16 -- C = A B with both inputs rounded to bfloat16 (to nearest
+ * even) and FP32 accumulation: the product the RQ_MIXED sketch B = Omega A
+ * uses (Sec. 3.1), for sketching other matrices the same way.
+ *   A     M x K (lda >= M), B  K x N (ldb >= K), C  M x N (ldc >= M, out):
+ *         FP32, column-major, device arrays owned by the caller; C must not
+ *         overlap A or B.
+ *   info  nullable device int32 (out): 0, or RQ_ETIMEOUT if a bounded wait of
+ *         the tensor-core kernel ran out.
+ * Products of bfloat16 values are exact in FP32.  On the tensor cores
+ * (tcgen05; A and B 16-byte aligned with lda, ldb multiples of 4) K is cut
+ * into chunks of at most 1024 whose results are added in IEEE FP32, since
+ * the tensor core's own accumulation is not round-to-nearest; otherwise CUDA
+ * cores accumulate each output in FP32 in K order.
+ * Errors: -(argument index) for M, N or K < 1, a NULL array or a short
+ * leading dimension (h is argument 1).  Asynchronous on stream.
+ */
+int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                 int ldc, int* info, rq_stream stream);
+
+/*
  * Tile policy of rq_tuxv_batched's block-level FP32 products.  A product with
  * M output rows and N output columns runs on 32 x 128 tiles when
  * M <= skinny_m, else on 128 x 32 tiles when N <= skinny_n, else on 64 x 64

@@ -1060,6 +1060,44 @@ int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems
   return RQ_OK;
 }
 
+int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                 int ldc, int* info, rq_stream stream) {
+  if (!valid(h)) return RQ_EHANDLE;
+  if (M < 1) return -2;
+  if (N < 1) return -3;
+  if (K < 1) return -4;
+  if (!A) return -5;
+  if (lda < M) return -6;
+  if (!B) return -7;
+  if (ldb < K) return -8;
+  if (!C) return -9;
+  if (ldc < M) return -10;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool tc = tc_gemm_supported(A, lda, B, ldb);
+  // split-K scratch on the tensor cores: one FP32 partial of C per chunk of
+  // at most 1024 K steps (the chunk rule of the tensor-core product)
+  const size_t chunks = (tc && K > 1024) ? (size_t)(K + 1023) / 1024 : 0;
+  const size_t split = chunks * sizeof(float) * (size_t)M * (size_t)N;
+  const int rc = ensure_ws(h, 256 + split);
+  if (rc) return rc;
+  char* base = static_cast<char*>(h->ws);
+  unsigned int* bar = reinterpret_cast<unsigned int*>(base);
+  int* err = reinterpret_cast<int*>(bar + 2);
+  Ctx c{st, h->num_sms, &h->launches, err, bar, chunks ? base + 256 : nullptr, split};
+  cudaError_t e;
+  {
+    Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * M * N * (double)K,
+             4.0 * ((double)M * K + (double)K * N + (double)M * N));
+    e = cudaMemsetAsync(bar, 0, 16, st);
+    if (e == cudaSuccess)
+      e = tc ? tc_gemm_nn_bf16(c, M, N, K, A, lda, B, ldb, C, ldc)
+             : gemm_bf16_inputs(c, M, N, K, A, lda, B, ldb, C, ldc);
+    if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, err, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "rq_gemm_bf16");
+  return RQ_OK;
+}
+
 int rq_set_batch_tiles(rq_handle h, const rq_batch_tiles* t) {
   if (!valid(h)) return RQ_EHANDLE;
   if (!t || t->skinny_m < 0 || t->skinny_n < 0) return -2;

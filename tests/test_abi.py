@@ -51,6 +51,7 @@ def test_null_handle_is_rejected(lib):
     assert L.rq_destroy(None) == _lib.RQ_EHANDLE
     assert L.rq_rqrcp(None, 0, 1, 1, None, 1, 1, 0, 1, None, 1, None, None, None, None) == _lib.RQ_EHANDLE
     assert L.rq_launch_count(None) == -1
+    assert L.rq_gemm_bf16(None, 4, 4, 4, None, 4, None, 4, None, 4, None, None) == _lib.RQ_EHANDLE
 
 
 def test_header_constants_match_the_binding():
