@@ -21,6 +21,11 @@
  *   word.
  * - The library owns only its workspace, held in the handle (see
  *   rq_workspace_size / rq_set_workspace).  No exception crosses the ABI.
+ * - A handle serves one host thread at a time (its workspace is not locked);
+ *   separate handles may be used from separate threads on separate streams at
+ *   once, as the continuous-batching server's lanes are.  Kernel launch
+ *   settings (shared-memory limits, occupancy) are taken once per process for
+ *   the device current at the first call: one GPU per process.
  *
  * Return codes: RQ_OK (0); -i when argument i (1-based, counting the handle
  * as argument 1) is invalid; or one of the named negative codes below.
