@@ -432,10 +432,16 @@ def leg_tuxv(h, steps=3, warmup=3, shape=(32768, 16384, 512)):
     err = float(torch.linalg.norm(R)) / na2 ** 0.5
     flops = 4.0 * k * m * n + 2.0 * (b + p) * m * n
     tr = prof["trailing"]
+    peak, peak_src = hbm_peak_gbs()
+    gbs = 4.0 * m * n * (2 + k // b) / (ms / 1e3) / 1e9
     out = {"workload": f"tuxv_mixed_lowrank_plus_noise_{m}x{n}_k{k}_b{b}_p{p}", "s": ms / 1e3,
            "tflops": flops / (ms / 1e3) / 1e12, "rel_error": err,
            "phases_ms": {kk: v[0] / steps for kk, v in prof.items()},
-           "hbm_bytes_algorithmic": 4.0 * m * n * (2 + k // b), "gbs_algorithmic": 4.0 * m * n * (2 + k // b) / (ms / 1e3) / 1e9,
+           # per phase: the algorithmic bytes and flops the library accounts, over the phase's event time
+           "phases_gbs": {kk: v[2] / (v[0] / 1e3) / 1e9 for kk, v in prof.items() if v[0] > 0 and v[2] > 0},
+           "phases_tflops": {kk: v[1] / (v[0] / 1e3) / 1e12 for kk, v in prof.items() if v[0] > 0 and v[1] > 0},
+           "hbm_bytes_algorithmic": 4.0 * m * n * (2 + k // b), "gbs_algorithmic": gbs,
+           "hbm_frac": gbs / peak, "hbm_peak_source": peak_src,
            "trailing_tflops": tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None}
     del A, A64, R
     return out
