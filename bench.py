@@ -495,7 +495,8 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True):
             ratios.append(float(np.linalg.norm(a - U @ X @ V.T)) / e_opt)
     return {"workload": f"batched_tuxv_mixed_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
             "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
-            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "info_nonzero": int((info != 0).sum()), **tuning,
+            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm_peak_gbs()[0],
+            "info_nonzero": int((info != 0).sum()), **tuning,
             "error_over_svd_optimum": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
                                        "max": float(np.max(ratios)) if ratios else None}}
 
