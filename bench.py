@@ -502,7 +502,7 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True):
 
 
 def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9,
-                tiles=None):
+                tiles=None, host=None, quality_sample=12):
     """Poisson arrivals of TUXV requests: the batch mix plus 10% 8192 x 4096, k = 256
     (tiles: the batched kernel's tile policy for the server's lanes)."""
     import numpy as np
@@ -532,7 +532,7 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
         gaps = g.exponential(1.0 / rate, size=n)
         t0 = time.perf_counter()
         tnext = t0
-        reqs = []
+        reqs, sources = [], []
         for i in range(n):
             tnext += gaps[i]
             dt = tnext - time.perf_counter()
@@ -540,11 +540,14 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
                 time.sleep(dt - 2e-4)
             while time.perf_counter() < tnext:
                 pass
+            src = None
             if g.random() < large_frac:
                 A, Om, b, p, k = big[i % len(big)]
             else:
-                A, Om, b, p, k = dev[int(g.integers(len(dev)))]
+                src = int(g.integers(len(dev)))
+                A, Om, b, p, k = dev[src]
             reqs.append(srv.submit(A, Om, b, p, k))
+            sources.append(src)
         for r in reqs:
             r.wait(120)
         srv.stop()
@@ -553,8 +556,23 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
         results.append(st_)
         torch.cuda.synchronize()
     sys.setswitchinterval(old_switch)
+    # quality of served results (last rate): rank-k error over the optimal rank-k
+    # error (numpy's SVD of the FP64 input) on a sample of the small requests
+    ratios = []
+    if host is not None:
+        small = [(r, j) for r, j in zip(reqs, sources) if j is not None
+                 and host[j][0].shape[0] * host[j][0].shape[1] <= 600 * 400]
+        for r, j in small[:quality_sample]:
+            a, k = host[j][0], host[j][4]
+            U, X, V = (t.cpu().double().numpy() for t in r.out)
+            sv = np.linalg.svd(a, compute_uv=False)
+            e_opt = float(np.sqrt(np.sum(sv[k:] ** 2)))
+            if e_opt > 0:
+                ratios.append(float(np.linalg.norm(a - U @ X @ V.T)) / e_opt)
     return {"workload": "poisson TUXV requests: 90% batch mix (m<=2048, n<=1024, k<=128), 10% 8192x4096 k=256",
-            "budget_gb": budget / 1e9, "by_rate": results}
+            "budget_gb": budget / 1e9, "by_rate": results,
+            "error_over_svd_optimum": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
+                                       "max": float(np.max(ratios)) if ratios else None}}
 
 
 def run_reference(args, ws, rank):
@@ -601,7 +619,7 @@ def main():
         return
     if args.only == "serving":
         host = batch_inputs(args.batch, seed=0)
-        print(json.dumps({"serving": leg_serving(to_device_f32(host))}), flush=True)
+        print(json.dumps({"serving": leg_serving(to_device_f32(host), host=host)}), flush=True)
         return
     if args.only == "tuxv":
         shape = tuple(int(x) for x in args.tuxv_shape.split(","))
@@ -824,7 +842,7 @@ def main():
             if "batched" in legs:
                 line["batched"] = leg_batched(h, host, dev, tune=not args.no_tune)
             if "serving" in legs:
-                line["serving"] = leg_serving(dev, tiles=line.get("batched", {}).get("tiles"))
+                line["serving"] = leg_serving(dev, tiles=line.get("batched", {}).get("tiles"), host=host)
             del dev
         except Exception as exc:  # a failing extra leg must not lose the headline line
             line["batched+serving"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
