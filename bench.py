@@ -243,6 +243,31 @@ def cpu_baseline(n, b, p, decades):
                       f"{dt:.1f} s; numpy with its BLAS threads"}
 
 
+def cpu_context(m=8192, n=4096, k=128, b=64, p=8, nq=4096):
+    """Host timings beside the CPU baseline, for context only (not targets):
+    the oracle's TUXV on the truncated workload's recipe scaled to m x n at
+    rank k (the size the oracle finishes in seconds), and LAPACK's unpivoted
+    and pivoted QR (dgeqrf, dgeqp3 through scipy; the paper's own comparison
+    routines) on an nq x nq graded matrix, with the host's BLAS threads."""
+    import scipy.linalg as sla
+    import oracle as O
+    from paper_2008_04447_gb300 import inputs as I
+    out = {"cores": os.cpu_count()}
+    a = I.lowrank_plus_noise(m, n, 1024, 1e-6, seed=3)
+    om = I.omega(b + p, m, seed=4)
+    t0 = time.perf_counter()
+    O.tuxv(a, om, b, k)
+    out[f"oracle_tuxv_{m}x{n}_k{k}_s"] = time.perf_counter() - t0
+    g = I.graded(nq, nq, 12, seed=5)
+    t0 = time.perf_counter()
+    sla.qr(g, mode="r", check_finite=False)
+    out[f"lapack_dgeqrf_{nq}_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sla.qr(g, mode="r", pivoting=True, check_finite=False)
+    out[f"lapack_dgeqp3_{nq}_s"] = time.perf_counter() - t0
+    return out
+
+
 def batch_inputs(count, seed, threads=16):
     """The many-small-problems workload: graded spectra 10^(-6 i/n), Haar factors,
     (m, n, k) from the batch recipe; generated on the host (FP64) in parallel."""
@@ -818,8 +843,10 @@ def main():
     if "cpu" in legs:
         try:
             line["cpu_baseline"] = cpu_baseline(args.cpu_n, b, p, args.decades)
+            line["cpu_context"] = cpu_context()
         except Exception as exc:  # a failing extra leg must not lose the headline line
-            line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            line.setdefault("cpu_baseline", {"error": f"{type(exc).__name__}: {exc}"[:300]})
+            line["cpu_context"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
             torch.cuda.empty_cache()
     del A0, A
     torch.cuda.empty_cache()

@@ -23,3 +23,10 @@ def test_fp64_peak_and_qr_flops():
     n = 16384
     assert abs(bench.flops_qr(n, n) / (4.0 * n ** 3 / 3.0) - 1.0) < 1e-14
     assert abs(bench.flops_qr(300, 200) / (2.0 * 300 * 200 ** 2 - 2.0 * 200 ** 3 / 3.0) - 1.0) < 1e-14
+
+
+def test_cpu_context_times_the_oracle_and_lapack():
+    out = bench.cpu_context(m=200, n=120, k=8, b=4, p=4, nq=64)
+    assert out["cores"] >= 1
+    for key in ("oracle_tuxv_200x120_k8_s", "lapack_dgeqrf_64_s", "lapack_dgeqp3_64_s"):
+        assert out[key] > 0.0
