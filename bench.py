@@ -791,6 +791,19 @@ def main():
             qr_ms = q0.elapsed_time(q1) / 2
             line["qr"] = {"s": qr_ms / 1e3, "tflops": fl / (qr_ms / 1e3) / 1e12,
                           "rqrcp_over_qr": ms_step / qr_ms, "clocks": qclk.stop()}
+            try:
+                # cuSOLVER's geqrf (through torch) on the same matrix, as context
+                torch.geqrf(A0)
+                torch.cuda.synchronize()
+                q0.record()
+                torch.geqrf(A0)
+                q1.record()
+                torch.cuda.synchronize()
+                g_ms = q0.elapsed_time(q1)
+                line["qr"].update({"cusolver_geqrf_s": g_ms / 1e3, "cusolver_geqrf_tflops": fl / (g_ms / 1e3) / 1e12,
+                                   "rqrcp_over_cusolver_geqrf": ms_step / g_ms})
+            except Exception as exc:  # context only
+                line["qr"]["cusolver_geqrf_error"] = f"{type(exc).__name__}: {exc}"[:200]
         except Exception as exc:  # a failing extra leg must not lose the headline line
             line["qr"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
             torch.cuda.empty_cache()
