@@ -24,17 +24,24 @@ def H():
     return build_and_handle()
 
 
-def test_rqrcp_fp64_16384_invariants(H):
+@pytest.fixture(scope="module")
+def graded16384():
+    """The 16384 x 16384 graded matrix (12 decades) and Omega of the benchmark,
+    FP64 column-major on the device, built once for the FP64 and FP32 cases."""
+    from paper_2008_04447_gb300 import colmajor
+    n, l = 16384, 72
+    return colmajor(I.graded_torch(n, n, 12, seed=0)), colmajor(I.omega_torch(l, n, seed=1000))
+
+
+def test_rqrcp_fp64_16384_invariants(H, graded16384):
     """jpvt is a permutation; every column of R has the norm of the pivoted
     column of A (Q is orthogonal; rounding grows like sqrt(m) eps, bound 1e-11
     relative); and the first block's pivots are the oracle's sample QRCP of the
     same sketch Omega A (formed here in FP64 by cuBLAS) up to the first decision
     with a relative gap below 1e-6 (the FP64 near-tie threshold)."""
     import torch
-    from paper_2008_04447_gb300 import colmajor
     n, b, p = 16384, 64, 8
-    A0 = colmajor(I.graded_torch(n, n, 12, seed=0))
-    Om = colmajor(I.omega_torch(b + p, n, seed=1000))
+    A0, Om = graded16384
     A = torch.empty_like(A0)
     A.copy_(A0)
     tau, jpvt, info = H.rqrcp(A, Om, b, p)
@@ -52,7 +59,7 @@ def test_rqrcp_fp64_16384_invariants(H):
     assert np.array_equal(jp[:upto], sq.perm[:upto])
 
 
-def test_rqrcp_fp32_16384_invariants(H):
+def test_rqrcp_fp32_16384_invariants(H, graded16384):
     """FP32 storage and 3xTF32 updates: the same invariants as the FP64 case
     with FP32 bounds -- column norms of R equal the pivoted columns' to 2e-4
     (about 10x sqrt(n) times FP32 rounding) and the first block's pivots equal
@@ -62,8 +69,8 @@ def test_rqrcp_fp32_16384_invariants(H):
     import torch
     from paper_2008_04447_gb300 import colmajor
     n, b, p = 16384, 64, 8
-    A0 = colmajor(I.graded_torch(n, n, 12, seed=0).float())
-    Om = colmajor(I.omega_torch(b + p, n, seed=1000, dtype=torch.float32))
+    A0 = colmajor(graded16384[0].float())
+    Om = colmajor(graded16384[1].float())
     A = torch.empty_like(A0)
     A.copy_(A0)
     tau, jpvt, info = H.rqrcp(A, Om, b, p)
