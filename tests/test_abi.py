@@ -70,3 +70,24 @@ def test_block_and_sample_limits_are_argument_errors(lib):
     assert L.rq_rqrcp_noalloc(0, 300, 300, x, 300, _lib.RQ_MAX_B + 1, 8, 10, x, 300, x, x, x, None) == -6
     assert L.rq_rqrcp_noalloc(0, 300, 300, x, 300, _lib.RQ_MAX_B, _lib.RQ_MAX_L - _lib.RQ_MAX_B + 1, 10, x, 400,
                               x, x, x, None) == -7
+
+
+def test_header_is_plain_c(lib, tmp_path):
+    """include/rqrcp.h compiles as C99 (pedantic, warnings as errors), a C
+    program links against the library, and its GPU-free calls agree with the
+    Python binding's."""
+    import subprocess
+    from paper_2008_04447_gb300 import _lib
+    src = os.path.join(ROOT, "tests", "native", "abi_c_check.c")
+    libdir = os.path.join(ROOT, "paper_2008_04447_gb300")
+    exe = str(tmp_path / "abi_c_check")
+    subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    src, "-o", exe, "-L", libdir, "-lrqrcp", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    rows = {r.split()[0]: r.split()[1:] for r in out if r.strip()}
+    assert rows["entry_points"] == [str(len(_declared())), "missing", "0"]
+    rc, prob = rows["latent_cdf"]
+    assert rc == "0" and abs(float(prob) - _lib.rq_latent_cdf(4, 0.125)) < 1e-6
+    assert rows["padding"] == ["0", str(_lib.rq_padding(0.125, 0.01))]
+    assert rows["tiles_search"] == ["0", "64", "16", "1.000", "16"]
+    assert rows["destroy_null"] == [str(_lib.RQ_EHANDLE)]
