@@ -54,7 +54,9 @@ def lookup(path: str, key: str):
 
 def store(path: str, key: str, tiles, ms) -> None:
     """Adds or replaces key's entry; the file is replaced atomically, so a
-    reader sees the old or the new contents, never a partial write."""
+    reader sees the old or the new contents, never a partial write.  Two
+    processes storing at once each read, add and replace: the later replace
+    wins and the other's new entry is lost (it is tuned again next time)."""
     d = _read(path)
     d[key] = {"tiles": [int(tiles[0]), int(tiles[1])], "ms": None if ms is None else float(ms)}
     folder = os.path.dirname(os.path.abspath(path))
