@@ -47,7 +47,7 @@ def lookup(path: str, key: str):
     if not isinstance(e, dict):
         return None
     t = e.get("tiles")
-    if not (isinstance(t, list) and len(t) == 2 and all(isinstance(v, int) and v >= 0 for v in t)):
+    if not (isinstance(t, list) and len(t) == 2 and all(type(v) is int and v >= 0 for v in t)):
         return None
     return {"tiles": t, "ms": e.get("ms")}
 

@@ -146,8 +146,8 @@ def test_cache_round_trip_and_unreadable_files(tmp_path):
     tuning.store(path, "k", (32, 32), 2.0)          # an unreadable file is replaced
     assert tuning.lookup(path, "k")["tiles"] == [32, 32]
     with open(path, "w") as f:
-        json.dump({"k": {"tiles": [-1, 3]}, "j": [1, 2]}, f)
-    assert tuning.lookup(path, "k") is None and tuning.lookup(path, "j") is None
+        json.dump({"k": {"tiles": [-1, 3]}, "j": [1, 2], "b": {"tiles": [True, 3]}}, f)
+    assert tuning.lookup(path, "k") is None and tuning.lookup(path, "j") is None and tuning.lookup(path, "b") is None
     assert not [f for f in os.listdir(tmp_path) if f.startswith(".tiles")]   # no temporary left behind
 
 
