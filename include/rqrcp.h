@@ -73,15 +73,23 @@ int rq_create(rq_handle* h);
  * caller must make sure no work that uses the handle is still running. */
 int rq_destroy(rq_handle h);
 
-/* Bytes of device workspace that operation `op` needs for these sizes. */
+/* Bytes of device workspace that operation `op` needs for these sizes:
+ * RQ_OP_RQRCP (rq_rqrcp), RQ_OP_RSRQRCP, RQ_OP_QR (k ignored), RQ_OP_TRQRCP
+ * and RQ_OP_TUXV (rq_tuxv and rq_tuxv_iter).  The batched call sizes its
+ * slots from its max_* bounds, rq_gemm_bf16 needs 256 bytes plus, on the
+ * tensor cores with K > 1024, 4 M N ceil(K / 1024) bytes, and
+ * rq_rqrcp_noalloc uses no handle. */
 int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b, int p,
                       size_t* bytes);
 
 /* Give the handle a caller-owned device workspace (NULL / 0 to go back to
- * library-managed workspace).  The caller keeps ownership and must keep it
- * alive while work issued through the handle runs.  A call whose need exceeds
- * a caller workspace returns RQ_ENOMEM.  Without a caller workspace the
- * library grows its own with cudaMalloc (synchronising the device). */
+ * library-managed workspace).  dptr must be 256-byte aligned, as cudaMalloc's
+ * are (the workspace holds FP64 arrays and tensor-map operands at 256-byte
+ * offsets from it): another address returns -2.  The caller keeps ownership
+ * and must keep it alive while work issued through the handle runs.  A call
+ * whose need exceeds a caller workspace returns RQ_ENOMEM before launching
+ * anything.  Without a caller workspace the library grows its own with
+ * cudaMalloc (synchronising the device). */
 int rq_set_workspace(rq_handle h, void* dptr, size_t bytes);
 
 /* Copy the last host-side error message of this handle into buf. */

@@ -791,6 +791,7 @@ int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b,
 
 int rq_set_workspace(rq_handle h, void* dptr, size_t bytes) {
   if (!valid(h)) return RQ_EHANDLE;
+  if (dptr && reinterpret_cast<uintptr_t>(dptr) % 256 != 0) return fail(h, -2, "workspace not 256-byte aligned");
   if (h->ws && h->ws_owned) cudaFree(h->ws);
   h->ws = dptr;
   h->ws_bytes = dptr ? bytes : 0;
