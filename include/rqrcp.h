@@ -328,7 +328,7 @@ int rq_tuxv_batched(rq_handle h, int prec, int count, const rq_problem* problems
  * uses (Sec. 3.1), for sketching other matrices the same way.
  *   A     M x K (lda >= M), B  K x N (ldb >= K), C  M x N (ldc >= M, out):
  *         FP32, column-major, device arrays owned by the caller; C must not
- *         overlap A or B.
+ *         overlap A or B (an overlap returns -9).
  *   info  nullable device int32 (out): 0, or RQ_ETIMEOUT if a bounded wait of
  *         the tensor-core kernel ran out.
  * Products of bfloat16 values are exact in FP32.  On the tensor cores

@@ -1073,6 +1073,15 @@ int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, cons
   if (ldb < K) return -8;
   if (!C) return -9;
   if (ldc < M) return -10;
+  {
+    // C may not overlap A or B (their column-major extents, in bytes)
+    const auto lo = [](const float* x) { return reinterpret_cast<uintptr_t>(x); };
+    const auto hi = [](const float* x, int ld, int rows, int cols) {
+      return reinterpret_cast<uintptr_t>(x) + sizeof(float) * ((size_t)ld * (cols - 1) + rows);
+    };
+    const uintptr_t c0 = lo(C), c1 = hi(C, ldc, M, N);
+    if ((c0 < hi(A, lda, M, K) && lo(A) < c1) || (c0 < hi(B, ldb, K, N) && lo(B) < c1)) return -9;
+  }
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool tc = tc_gemm_supported(A, lda, B, ldb);
   // split-K scratch on the tensor cores: one FP32 partial of C per chunk of

@@ -50,3 +50,8 @@ def test_gemm_bf16_argument_checks(H):
     assert _lib.rq_gemm_bf16(H.h, 4, 4, 4, x, 3, x, 4, x, 4) == -6
     assert _lib.rq_gemm_bf16(H.h, 4, 4, 4, x, 4, x, 3, x, 4) == -8
     assert _lib.rq_gemm_bf16(H.h, 4, 4, 4, x, 4, x, 4, None, 4) == -9
+    y = torch.zeros(64, device="cuda")
+    assert _lib.rq_gemm_bf16(H.h, 4, 4, 4, y, 4, y[16:], 4, y[8:], 4) == -9       # C overlaps A and B
+    # disjoint (A starts one float in: not 16-byte aligned, so the CUDA-core path)
+    assert _lib.rq_gemm_bf16(H.h, 4, 4, 4, y[1:], 4, y[20:], 4, y[40:], 4) == 0
+    torch.cuda.synchronize()
