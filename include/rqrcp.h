@@ -247,7 +247,9 @@ int rq_qr(rq_handle h, int prec, int m, int n, void* A, int lda, int b, void* ta
  *   Y   m x k (ldy >= m, out): reflectors, unit diagonal, zeros above.
  *   tau k (out).
  *   R   k x n (ldr >= k, out): upper trapezoidal, pivoted column order.
- *   jpvt, info as for rq_rqrcp.
+ *   b, p, k, Omega, jpvt, info as for rq_rqrcp.
+ * Precisions: RQ_FP64, RQ_FP32 and RQ_MIXED (the sketch from bfloat16-rounded
+ * Omega and A, FP32 accumulation).
  */
 int rq_trqrcp(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k,
               const void* Omega, int ldo, void* Y, int ldy, void* tau, void* R, int ldr, int* jpvt,
@@ -262,6 +264,8 @@ int rq_trqrcp(rq_handle h, int prec, int m, int n, const void* A, int lda, int b
  *   sigma NULL, or k entries (out): the singular values of X from a one-sided
  *         Jacobi SVD (descending); U and V are then rotated by the core
  *         singular vectors and X is returned as diag(sigma).
+ *   b, p, k, Omega, info as for rq_trqrcp; precisions as rq_trqrcp (the core
+ *   SVD in FP64 in every mode).
  */
 int rq_tuxv(rq_handle h, int prec, int m, int n, const void* A, int lda, int b, int p, int k,
             const void* Omega, int ldo, void* U, int ldu, void* X, int ldx, void* V, int ldv,
