@@ -119,13 +119,14 @@ class Server:
             r.admitted = now
             m, n = r.A.shape
             torch = self.torch
-            try:
-                r.out = (torch.empty((r.k, m), dtype=r.A.dtype, device=self.device).t(),
-                         torch.empty((r.k, r.k), dtype=r.A.dtype, device=self.device).t(),
-                         torch.empty((r.k, n), dtype=r.A.dtype, device=self.device).t())
-            except RuntimeError as exc:  # the device ran out of memory below the budget
-                self._fail([r], exc, now)
-                continue
+            if not r.large:              # a large request gets its outputs from rq_tuxv at launch
+                try:
+                    r.out = (torch.empty((r.k, m), dtype=r.A.dtype, device=self.device).t(),
+                             torch.empty((r.k, r.k), dtype=r.A.dtype, device=self.device).t(),
+                             torch.empty((r.k, n), dtype=r.A.dtype, device=self.device).t())
+                except RuntimeError as exc:  # the device ran out of memory below the budget
+                    self._fail([r], exc, now)
+                    continue
             self.ready.append(r)
 
     def _reap(self, now):
