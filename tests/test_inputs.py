@@ -35,3 +35,20 @@ def test_batch_shapes():
     sh = I.batch_shapes(500, seed=0)
     for m, n, k in sh:
         assert 64 <= m <= 2048 and 1 <= n <= min(m, 1024) and 1 <= k <= min(m, n) // 2
+
+
+def test_lowrank_parts_rebuild_the_matrix_exactly():
+    """The parts (Haar U, sigma_i = i^-2, Haar V, noise) come from the same
+    generator in the same order as the matrix itself, so (U s) V^T + noise
+    reproduces it bit for bit (the full-size TUXV test relies on it)."""
+    import torch
+    from paper_2008_04447_gb300 import inputs as I
+    for args in [(300, 200, 64, 1e-6, 7), (120, 90, 200, 0.0, 3)]:
+        a = I.lowrank_plus_noise_torch(*args, device="cpu")
+        u, s, v, nz = I.lowrank_plus_noise_parts_torch(*args, device="cpu")
+        b = (u * s) @ v.T
+        if nz is not None:
+            b += nz
+        assert torch.equal(a, b)
+        assert (nz is None) == (args[3] == 0.0)
+        assert torch.equal(s, torch.arange(1, s.numel() + 1, dtype=torch.float64) ** -2.0)
