@@ -22,8 +22,16 @@ __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
 
 
 def colmajor(x):
-    """Column-major (Fortran-order) copy of a 2-D tensor: stride (1, rows)."""
-    return x.t().contiguous().t()
+    """Column-major (Fortran-order) copy of a 2-D tensor: strides (1, rows).
+
+    The copy goes into a tensor allocated as (cols, rows) and transposed, so a
+    single-row matrix also gets stride 1 between rows and 1 between columns
+    (``x.t().contiguous()`` would keep a 1 x N tensor's row-major strides,
+    because torch does not count the stride of a size-1 dimension)."""
+    import torch
+    out = torch.empty((x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device).t()
+    out.copy_(x)
+    return out
 
 
 def _prec_of(t):
@@ -36,7 +44,15 @@ def _prec_of(t):
 
 
 def _ld(t):
-    if t.dim() != 2 or t.stride(0) != 1:
+    """Leading dimension of a column-major 2-D tensor (entry (i, j) at i + j ld).
+
+    A single-row matrix has no row stride to check: any stride(0) is accepted
+    and ld is its column stride (at least 1)."""
+    if t.dim() != 2:
+        raise ValueError("column-major matrix expected (stride (1, ld)); use colmajor()")
+    if t.shape[0] == 1:
+        return max(t.stride(1), 1)
+    if t.stride(0) != 1:
         raise ValueError("column-major matrix expected (stride (1, ld)); use colmajor()")
     return max(t.stride(1), t.shape[0], 1)
 

@@ -96,7 +96,7 @@ def test_header_is_plain_c(lib, tmp_path):
 def test_gemm_bf16_rejects_an_output_overlapping_its_inputs(lib):
     """The overlap check runs on the host before any CUDA call, so it needs a
     handle only for its validity check: with NULL it is RQ_EHANDLE, and the
-    overlap rule is exercised on a GPU in tests/test_zzz_gemm.py."""
+    overlap rule is exercised on a GPU in tests/test_gpu_gemm_bf16.py."""
     from paper_2008_04447_gb300 import _lib
     L = _lib.load()
     assert L.rq_gemm_bf16(None, 4, 4, 4, 4096, 4, 8192, 4, 4096, 4, None, None) == _lib.RQ_EHANDLE
