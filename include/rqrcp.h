@@ -413,6 +413,21 @@ int rq_tune_batched(rq_handle h, int prec, int count, const rq_problem* problems
                     int max_b, int max_p, int reps, int passes, rq_stream stream, rq_batch_tiles* best,
                     double* best_ms);
 
+/*
+ * rq_selftest_wait_timeout -- failure-detection self-test (the paper has no
+ * counterpart).  Every wait on another CTA in this library is bounded: when
+ * an arrival does not come within about a second or two, the kernel writes
+ * RQ_ETIMEOUT to the call's info word and returns, leaving the CUDA context
+ * usable.  This call launches two CTAs at the library's grid barrier with a
+ * count of three, so their wait can only run out; once the stream reaches it,
+ * *info == RQ_ETIMEOUT.
+ *   bar   device array of 2 uint32 owned by the caller (zeroed by the call).
+ *   info  device int32 (out): zeroed, then RQ_ETIMEOUT.
+ * Errors: -1 / -2 for a NULL bar / info; RQ_ECUDA if the launch fails.
+ * Asynchronous on stream.
+ */
+int rq_selftest_wait_timeout(unsigned int* bar, int* info, rq_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ _SIGS = {
     "rq_latent_cdf": ([_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], _I),
     "rq_padding": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], _I),
     "rq_gaussian": ([_P, _I, ctypes.c_uint64, ctypes.c_uint64, _I, _I, _P, _I, _P], _I),
+    "rq_selftest_wait_timeout": ([_P, _P, _P], _I),
 }
 
 # rq_problem: twelve int32 then seven 64-bit device pointers (104 bytes)
@@ -182,6 +183,10 @@ def rq_rqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream
 def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
     return load().rq_rqrcp_noalloc(prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
                                    _ptr(info), _stream(stream))
+
+
+def rq_selftest_wait_timeout(bar, info, stream=None):
+    return load().rq_selftest_wait_timeout(_ptr(bar), _ptr(info), _stream(stream))
 
 
 def rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p, stream=None):
