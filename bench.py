@@ -53,11 +53,11 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--decades", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg but the timed RQRCP")
-    ap.add_argument("--legs", default="qr,e2e,fp32,rsrqrcp,cpu,slices,tuxv,batched,serving",
+    ap.add_argument("--legs", default="qr,e2e,fp32,rsrqrcp,cpu,fp64peak,slices,tuxv,batched,serving",
                     help="extra legs to run (comma list); --no-extras clears it")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="precision of the timed RQRCP")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
-    ap.add_argument("--only", default="", choices=["", "tuxv", "batched", "serving"],
+    ap.add_argument("--only", default="", choices=["", "tuxv", "batched", "serving", "fp64peak"],
                     help="run only this leg and print its JSON (profiling)")
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched leg")
@@ -426,95 +426,159 @@ def leg_slices(h):
     return out
 
 
+def leg_fp64_peak(n=8192, reps=3):
+    """FP64 throughput of cuBLAS DGEMM (through torch) on n x n operands, timed
+    with CUDA events with the SM clocks sampled: a measured reference for the
+    FP64 trailing update's derived peak (152 SMs x 2 DFMA/clk x 2 flop x clock)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(reps):
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    best = min(times)
+    del a, b, c
+    return {"cublas_dgemm_tflops": 2.0 * n ** 3 / (best / 1e3) / 1e12, "n": n, "ms": best,
+            "derived_peak_tflops": FP64_PEAK_TFLOPS, "clocks": clocks}
+
+
 def leg_tuxv(h, steps=3, warmup=3, shape=(32768, 16384, 512)):
     """Truncated RQRCP + TUXV of one m x n matrix (low rank + noise; default
-    32768 x 16384, k = 512), mixed precision."""
+    32768 x 16384, k = 512): the FP32 path (FP32 sketch; the reduced-precision
+    path that keeps each rank-k error within 1.05x the FP64 oracle's) and,
+    beside it, the mixed mode (sketch from bfloat16-rounded inputs)."""
     import torch
-    from paper_2008_04447_gb300 import RQ_MIXED, colmajor
+    from paper_2008_04447_gb300 import RQ_FP32, RQ_MIXED, colmajor
     from paper_2008_04447_gb300 import inputs as I
     m, n, k = shape
     b, p = 64, 8
     A = colmajor(I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7).float())
     Om = colmajor(I.omega_torch(b + p, m, seed=8, dtype=torch.float32))
-    for _ in range(warmup):
-        h.tuxv(A, Om, b, p, k, prec=RQ_MIXED)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h.profile(True)
-    e0.record()
-    for _ in range(steps):
-        U, X, V, _, info = h.tuxv(A, Om, b, p, k, prec=RQ_MIXED)
-    e1.record()
-    torch.cuda.synchronize()
-    prof = h.profile_read()
-    h.profile(False)
-    ms = e0.elapsed_time(e1) / steps
-    # rank-k error in FP64 against the FP64 input: ||A||^2 - ||X||^2 (A V V^T is a projection)
-    A64 = I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7)
-    na2 = float((A64 * A64).sum())
-    Ud, Xd, Vd = U.double(), X.double(), V.double()
-    R = A64 - Ud @ (Xd @ Vd.T)
-    err = float(torch.linalg.norm(R)) / na2 ** 0.5
-    flops = 4.0 * k * m * n + 2.0 * (b + p) * m * n
-    tr = prof["trailing"]
     peak, peak_src = hbm_peak_gbs()
-    gbs = 4.0 * m * n * (2 + k // b) / (ms / 1e3) / 1e9
-    out = {"workload": f"tuxv_mixed_lowrank_plus_noise_{m}x{n}_k{k}_b{b}_p{p}", "s": ms / 1e3,
-           "tflops": flops / (ms / 1e3) / 1e12, "rel_error": err,
-           "phases_ms": {kk: v[0] / steps for kk, v in prof.items()},
-           # per phase: the algorithmic bytes and flops the library accounts, over the phase's event time
-           "phases_gbs": {kk: v[2] / (v[0] / 1e3) / 1e9 for kk, v in prof.items() if v[0] > 0 and v[2] > 0},
-           "phases_tflops": {kk: v[1] / (v[0] / 1e3) / 1e12 for kk, v in prof.items() if v[0] > 0 and v[1] > 0},
-           "hbm_bytes_algorithmic": 4.0 * m * n * (2 + k // b), "gbs_algorithmic": gbs,
-           "hbm_frac": gbs / peak, "hbm_peak_source": peak_src,
-           "trailing_tflops": tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None}
-    del A, A64, R
+    flops = 4.0 * k * m * n + 2.0 * (b + p) * m * n
+    byts = 4.0 * m * n * (2 + k // b)
+
+    def arm(prec):
+        for _ in range(warmup):
+            h.tuxv(A, Om, b, p, k, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h.profile(True)
+        e0.record()
+        for _ in range(steps):
+            U, X, V, _, info = h.tuxv(A, Om, b, p, k, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = h.profile_read()
+        h.profile(False)
+        ms = e0.elapsed_time(e1) / steps
+        gbs = byts / (ms / 1e3) / 1e9
+        tr = prof["trailing"]
+        return {"s": ms / 1e3, "tflops": flops / (ms / 1e3) / 1e12, "info": int(info.abs().sum()),
+                "phases_ms": {kk: v[0] / steps for kk, v in prof.items()},
+                # per phase: the algorithmic bytes and flops the library accounts, over the phase's event time
+                "phases_gbs": {kk: v[2] / (v[0] / 1e3) / 1e9 for kk, v in prof.items() if v[0] > 0 and v[2] > 0},
+                "phases_tflops": {kk: v[1] / (v[0] / 1e3) / 1e12 for kk, v in prof.items() if v[0] > 0 and v[1] > 0},
+                "gbs_algorithmic": gbs, "hbm_frac": gbs / peak,
+                "trailing_tflops": tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None}, (U, X, V)
+
+    out = {"workload": f"tuxv_lowrank_plus_noise_{m}x{n}_k{k}_b{b}_p{p}", "hbm_bytes_algorithmic": byts,
+           "hbm_peak_source": peak_src}
+    res = {}
+    for name, prec in (("fp32", RQ_FP32), ("mixed", RQ_MIXED)):
+        out[name], res[name] = arm(prec)
+    # rank-k error in FP64 against the FP64 input
+    A64 = I.lowrank_plus_noise_torch(m, n, 2048, 1e-6, seed=7)
+    for name, (U, X, V) in res.items():
+        R = A64 - U.double() @ (X.double() @ V.double().T)
+        out[name]["rel_error"] = float(torch.linalg.norm(R) / torch.linalg.norm(A64))
+        del R
+    out["mixed_over_fp32_time"] = out["mixed"]["s"] / out["fp32"]["s"]
+    del A, A64, res
     return out
 
 
-def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True):
-    """4096 uneven problems in one persistent launch (mixed precision).
+def _rank_k_errors(host, order, idx, outs_by_arm, limit=600 * 400):
+    """Per sampled problem: the rank-k error ||A - U X V^T||_F / ||A||_F of each
+    arm's result, in FP64 against the FP64 input (problems of at most limit
+    entries)."""
+    import numpy as np
+    rows = []
+    for j in idx:
+        a = host[order[j]][0]
+        if a.shape[0] * a.shape[1] > limit:
+            continue
+        na = float(np.linalg.norm(a))
+        row = {}
+        for arm, outs in outs_by_arm.items():
+            U, X, V = (t.cpu().double().numpy() for t in outs[j][:3])
+            row[arm] = float(np.linalg.norm(a - U @ X @ V.T)) / na
+        rows.append(row)
+    return rows
 
-    With tune, the tile policy is autotuned on the batch first (outside the
-    timed region; every policy gives the same bits).  Quality: on a sample of
-    problems, the rank-k error over the optimal rank-k error of the FP64 input
-    (numpy's SVD); the comparison with the oracle is the GPU tests' job."""
+
+def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True, fp64=True):
+    """4096 uneven problems in one persistent launch: the FP32 path (tile policy
+    autotuned on the batch first, outside the timed region; every policy gives
+    the same bits), the mixed mode beside it, and the plain FP64 path (rq_tuxv
+    in FP64, problem after problem: the batched kernel is FP32-only).
+
+    Quality, per sampled problem: each reduced-precision result's rank-k error
+    over the FP64 path's on the same problem (the FP64 path matches the oracle
+    to 1e-12 in the tests), and over the optimal rank-k error (numpy's SVD of
+    the FP64 input)."""
     import numpy as np
     import torch
-    from paper_2008_04447_gb300 import RQ_MIXED
+    from paper_2008_04447_gb300 import RQ_FP32, RQ_MIXED
     order = sorted(range(len(dev)), key=lambda i: -(dev[i][0].shape[0] * dev[i][0].shape[1] * dev[i][4]))
     probs = [dev[i] for i in order]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tuning = {"tiles": list(h.batch_tiles)}
     outs = None
     if tune:
         try:
             t0 = time.perf_counter()
-            tiles, tuned_ms, outs, _ = h.tune_batched(probs, prec=RQ_MIXED, reps=1, passes=2)
+            tiles, tuned_ms, outs, _ = h.tune_batched(probs, prec=RQ_FP32, reps=1, passes=2)
             tuning = {"tiles": list(tiles), "tune_s": time.perf_counter() - t0, "tuned_ms": tuned_ms}
         except Exception as exc:  # the policy stays as it was; the leg is still measured
             tuning["tune_error"] = f"{type(exc).__name__}: {exc}"[:200]
-    outs, info = h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
-    for _ in range(warmup - 1):
-        h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        outs, info = h.tuxv_batched(probs, prec=RQ_MIXED, outputs=outs)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed(prec, outs):
+        outs, info = h.tuxv_batched(probs, prec=prec, outputs=outs)
+        for _ in range(warmup - 1):
+            h.tuxv_batched(probs, prec=prec, outputs=outs)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            outs, info = h.tuxv_batched(probs, prec=prec, outputs=outs)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, outs, info
+
+    ms, outs, info = timed(RQ_FP32, outs)
+    mms, mouts, minfo = timed(RQ_MIXED, None)
     # the same launch captured once in a CUDA graph and replayed (the call issues
     # one memset and one kernel, so the graph mainly removes host work)
     graph = {}
     try:
         from paper_2008_04447_gb300 import rq_tuxv_batched
+        outs, info = h.tuxv_batched(probs, prec=RQ_FP32, outputs=outs)
         desc = h._keep                     # the descriptors of the last call (outputs = outs)
         dims = (max(int(t[0].shape[0]) for t in probs), max(int(t[0].shape[1]) for t in probs),
                 max(int(t[4]) for t in probs), max(int(t[2]) for t in probs), max(int(t[3]) for t in probs))
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            rc = rq_tuxv_batched(h.h, RQ_MIXED, len(probs), desc, *dims)
+            rc = rq_tuxv_batched(h.h, RQ_FP32, len(probs), desc, *dims)
         if rc != 0:
             raise RuntimeError(f"rq_tuxv_batched failed under capture with status {rc}")
         g.replay()
@@ -530,37 +594,66 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True):
         graph = {"graph_error": f"{type(exc).__name__}: {exc}"[:200]}
     flops = sum(4.0 * k * A.shape[0] * A.shape[1] + 2.0 * (b + p) * A.shape[0] * A.shape[1] for A, Om, b, p, k in probs)
     byts = sum(4.0 * A.shape[0] * A.shape[1] * (3 + (k + b - 1) // b) for A, Om, b, p, k in probs)
-    # rank-k error over the optimal rank-k error (Eckart-Young) on a sample of problems
-    ratios = []
+    out = {"workload": f"batched_tuxv_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
+           "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
+           "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm_peak_gbs()[0],
+           "info_nonzero": int((info != 0).sum()), **tuning, **graph,
+           "mixed": {"s": mms / 1e3, "problems_per_s": len(probs) / (mms / 1e3), "info_nonzero": int((minfo != 0).sum())}}
     g = np.random.default_rng(0)
-    for j in g.choice(len(probs), size=min(quality_sample, len(probs)), replace=False):
-        a, om, b, p, k = host[order[j]]
-        if a.shape[0] * a.shape[1] > 600 * 400:
-            continue
-        U, X, V = (t.cpu().double().numpy() for t in outs[j])
+    idx = g.choice(len(probs), size=min(quality_sample, len(probs)), replace=False)
+    arms = {"fp32": outs, "mixed": mouts}
+    if fp64:
+        # the plain FP64 path: rq_tuxv in FP64 on every problem, one after another
+        import torch as _t
+        from paper_2008_04447_gb300 import colmajor
+        d64 = [(colmajor(_t.as_tensor(host[i][0])).cuda(), colmajor(_t.as_tensor(host[i][1])).cuda(),
+                host[i][2], host[i][3], host[i][4]) for i in order]
+        for A, Om, b, p, k in d64[:16]:
+            h.tuxv(A, Om, b, p, k)
+        _t.cuda.synchronize()
+        e0.record()
+        o64 = [h.tuxv(A, Om, b, p, k)[:3] for A, Om, b, p, k in d64]
+        e1.record()
+        _t.cuda.synchronize()
+        f64ms = e0.elapsed_time(e1)
+        out["fp64"] = {"s": f64ms / 1e3, "problems_per_s": len(probs) / (f64ms / 1e3),
+                       "path": "rq_tuxv FP64 per problem, one stream"}
+        out["fp32_over_fp64_throughput"] = f64ms / ms
+        arms["fp64"] = o64
+    rows = _rank_k_errors(host, order, idx, arms)
+    if fp64 and rows:
+        r32 = [r["fp32"] / r["fp64"] for r in rows if r["fp64"] > 0]
+        rmx = [r["mixed"] / r["fp64"] for r in rows if r["fp64"] > 0]
+        out["error_over_fp64_path"] = {"n": len(r32), "fp32_max": max(r32), "fp32_median": float(np.median(r32)),
+                                       "mixed_max": max(rmx), "mixed_median": float(np.median(rmx))}
+    # rank-k error over the optimal rank-k error (Eckart-Young) of the FP32 results
+    opt = []
+    for j, row in zip([j for j in idx if host[order[j]][0].size <= 600 * 400], rows):
+        a, k = host[order[j]][0], host[order[j]][4]
         sv = np.linalg.svd(a, compute_uv=False)
-        e_opt = float(np.sqrt(np.sum(sv[k:] ** 2)))
+        e_opt = float(np.sqrt(np.sum(sv[k:] ** 2))) / float(np.linalg.norm(a))
         if e_opt > 0:
-            ratios.append(float(np.linalg.norm(a - U @ X @ V.T)) / e_opt)
-    return {"workload": f"batched_tuxv_mixed_{len(probs)}_problems", "problems": len(probs), "s": ms / 1e3,
-            "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
-            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm_peak_gbs()[0],
-            "info_nonzero": int((info != 0).sum()), **tuning, **graph,
-            "error_over_svd_optimum": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
-                                       "max": float(np.max(ratios)) if ratios else None}}
+            opt.append(row["fp32"] / e_opt)
+    out["error_over_svd_optimum"] = {"n": len(opt), "median": float(np.median(opt)) if opt else None,
+                                     "max": float(np.max(opt)) if opt else None}
+    return out
 
 
 def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large_frac=0.1, budget=120e9,
-                tiles=None, host=None, quality_sample=12):
+                tiles=None, host=None, quality_sample=12, prec=None):
     """Poisson arrivals of TUXV requests: the batch mix plus 10% 8192 x 4096, k = 256
-    (tiles: the batched kernel's tile policy for the server's lanes)."""
+    (tiles: the batched kernel's tile policy for the server's lanes).  prec:
+    RQ_FP32 (default; small requests batched, large ones through rq_tuxv) or
+    RQ_FP64 (dev then holds FP64 inputs; every request through rq_tuxv)."""
     import numpy as np
     import torch
-    from paper_2008_04447_gb300 import colmajor
+    from paper_2008_04447_gb300 import RQ_FP32, RQ_FP64, Handle, colmajor
     from paper_2008_04447_gb300 import inputs as I
     from paper_2008_04447_gb300.serve import Server
-    big = [(colmajor(I.lowrank_plus_noise_torch(8192, 4096, 1024, 1e-6, seed=40 + i).float()),
-            colmajor(I.omega_torch(72, 8192, seed=50 + i, dtype=torch.float32)), 64, 8, 256) for i in range(2)]
+    prec = RQ_FP32 if prec is None else prec
+    dt_big = torch.float64 if prec == RQ_FP64 else torch.float32
+    big = [(colmajor(I.lowrank_plus_noise_torch(8192, 4096, 1024, 1e-6, seed=40 + i).to(dt_big)),
+            colmajor(I.omega_torch(72, 8192, seed=50 + i, dtype=dt_big)), 64, 8, 256) for i in range(2)]
     import sys
     results = []
     g = np.random.default_rng(1)
@@ -570,11 +663,12 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
     old_switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)
     for rate in rates:
-        srv = Server(budget_bytes=budget, lanes=3, tiles=tiles)
+        srv = Server(budget_bytes=budget, lanes=3, tiles=tiles, prec=prec)
         # warm the lanes' workspaces
         for lane_h, st in srv.lanes:
-            lane_h.tuxv_batched(dev[:8], stream=st)
-            lane_h.tuxv(*big[0][:2], 64, 8, 256, stream=st)
+            if prec != RQ_FP64:
+                lane_h.tuxv_batched(dev[:8], stream=st, prec=prec)
+            lane_h.tuxv(*big[0][:2], 64, 8, 256, stream=st, prec=prec)
         torch.cuda.synchronize()
         srv.start()
         n = max(20, int(rate * seconds))
@@ -598,30 +692,46 @@ def leg_serving(dev, rates=(100, 200, 500, 1000, 2000, 5000), seconds=1.0, large
             reqs.append(srv.submit(A, Om, b, p, k))
             sources.append(src)
         for r in reqs:
-            r.wait(120)
+            r.wait(300)
         srv.stop()
         st_ = srv.stats()
         st_["offered_rate"] = rate
         results.append(st_)
         torch.cuda.synchronize()
     sys.setswitchinterval(old_switch)
-    # quality of served results (last rate): rank-k error over the optimal rank-k
-    # error (numpy's SVD of the FP64 input) on a sample of the small requests
-    ratios = []
-    if host is not None:
+    out = {"workload": "poisson TUXV requests: 90% batch mix (m<=2048, n<=1024, k<=128), 10% 8192x4096 k=256",
+           "prec": {RQ_FP32: "fp32", RQ_FP64: "fp64"}.get(prec, str(prec)), "budget_gb": budget / 1e9,
+           "by_rate": results}
+    # quality of served results (last rate), on a sample of the small requests:
+    # the rank-k error (FP64, against the FP64 input) over that of the FP64 path
+    # (rq_tuxv in FP64 on the same problem) and over the optimal rank-k error
+    # (numpy's SVD of the FP64 input)
+    if host is not None and prec != RQ_FP64:
+        h64 = Handle()
+        r64, ropt = [], []
         small = [(r, j) for r, j in zip(reqs, sources) if j is not None
                  and host[j][0].shape[0] * host[j][0].shape[1] <= 600 * 400]
         for r, j in small[:quality_sample]:
-            a, k = host[j][0], host[j][4]
+            a, om, b, p, k = host[j]
+            na = float(np.linalg.norm(a))
             U, X, V = (t.cpu().double().numpy() for t in r.out)
+            e = float(np.linalg.norm(a - U @ X @ V.T)) / na
+            U6, X6, V6, _, _ = h64.tuxv(colmajor(torch.as_tensor(a)).cuda(), colmajor(torch.as_tensor(om)).cuda(),
+                                        b, p, k)
+            U6, X6, V6 = (t.cpu().numpy() for t in (U6, X6, V6))
+            e64 = float(np.linalg.norm(a - U6 @ X6 @ V6.T)) / na
             sv = np.linalg.svd(a, compute_uv=False)
-            e_opt = float(np.sqrt(np.sum(sv[k:] ** 2)))
+            e_opt = float(np.sqrt(np.sum(sv[k:] ** 2))) / na
+            if e64 > 0:
+                r64.append(e / e64)
             if e_opt > 0:
-                ratios.append(float(np.linalg.norm(a - U @ X @ V.T)) / e_opt)
-    return {"workload": "poisson TUXV requests: 90% batch mix (m<=2048, n<=1024, k<=128), 10% 8192x4096 k=256",
-            "budget_gb": budget / 1e9, "by_rate": results,
-            "error_over_svd_optimum": {"n": len(ratios), "median": float(np.median(ratios)) if ratios else None,
-                                       "max": float(np.max(ratios)) if ratios else None}}
+                ropt.append(e / e_opt)
+        h64.close()
+        out["error_over_fp64_path"] = {"n": len(r64), "median": float(np.median(r64)) if r64 else None,
+                                       "max": float(np.max(r64)) if r64 else None}
+        out["error_over_svd_optimum"] = {"n": len(ropt), "median": float(np.median(ropt)) if ropt else None,
+                                         "max": float(np.max(ropt)) if ropt else None}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -669,6 +779,9 @@ def main():
     if args.only == "serving":
         host = batch_inputs(args.batch, seed=0)
         print(json.dumps({"serving": leg_serving(to_device_f32(host), host=host)}), flush=True)
+        return
+    if args.only == "fp64peak":
+        print(json.dumps({"fp64_peak": leg_fp64_peak()}), flush=True)
         return
     if args.only == "tuxv":
         shape = tuple(int(x) for x in args.tuxv_shape.split(","))
@@ -887,6 +1000,14 @@ def main():
             torch.cuda.empty_cache()
     del A0, A
     torch.cuda.empty_cache()
+    if "fp64peak" in legs:
+        try:
+            pk = leg_fp64_peak()
+            line["fp64_peak"] = pk
+            if args.prec == "fp64" and achieved:
+                roofline["frac_of_cublas_dgemm"] = achieved / pk["cublas_dgemm_tflops"]
+        except Exception as exc:  # context only
+            line["fp64_peak"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     if "slices" in legs:
         try:
             line["slices"] = leg_slices(h)
@@ -908,6 +1029,21 @@ def main():
             if "serving" in legs:
                 line["serving"] = leg_serving(dev, tiles=line.get("batched", {}).get("tiles"), host=host)
             del dev
+            torch.cuda.empty_cache()
+            if "serving" in legs:
+                # the plain FP64 path under the same arrivals (every request through rq_tuxv)
+                from paper_2008_04447_gb300 import RQ_FP64
+                d64 = [(colmajor(torch.as_tensor(a)).cuda(), colmajor(torch.as_tensor(om)).cuda(), bb, pp, kk)
+                       for a, om, bb, pp, kk in host]
+                s64 = leg_serving(d64, rates=(100, 500, 1000), prec=RQ_FP64)
+                line["serving"]["fp64"] = s64
+                by32 = {r["offered_rate"]: r for r in line["serving"]["by_rate"]}
+                line["serving"]["fp32_over_fp64"] = [
+                    {"offered_rate": r["offered_rate"],
+                     "req_per_s": by32[r["offered_rate"]]["req_per_s"] / r["req_per_s"],
+                     "p99": by32[r["offered_rate"]]["p99_ms"] / r["p99_ms"]}
+                    for r in s64["by_rate"] if r["offered_rate"] in by32]
+                del d64
         except Exception as exc:  # a failing extra leg must not lose the headline line
             line["batched+serving"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
             torch.cuda.empty_cache()

@@ -4,7 +4,9 @@ Requests (A, Omega, b, p, k) arrive at any time.  The server admits them
 against an HBM byte budget (inputs, outputs and their share of the scratch),
 packs every admitted small request into the next batched launch
 (``rq_tuxv_batched``: one persistent kernel over uneven problems) and sends
-large ones to the whole-GPU ``rq_tuxv``.  Up to ``lanes`` launches are on the
+large ones to the whole-GPU ``rq_tuxv``.  In FP64 (``prec=RQ_FP64``, the plain
+FP64 path, which the batched kernel does not provide) every request goes to
+``rq_tuxv``.  Up to ``lanes`` launches are on the
 GPU at once, each on its own CUDA stream with its own library handle, so
 requests that arrive while others run start as soon as a lane and memory free
 up, and their work overlaps on the device.  A request's result does not
@@ -21,7 +23,7 @@ import threading
 import time
 from dataclasses import dataclass, field
 
-from . import RQ_FP32, RQ_MIXED, Handle
+from . import RQ_FP32, RQ_FP64, Handle
 
 __all__ = ["Request", "Server", "footprint_bytes"]
 
@@ -71,9 +73,12 @@ class Request:
 class Server:
     """Admission + continuous batching over ``lanes`` concurrent GPU launches."""
 
-    def __init__(self, budget_bytes=120e9, lanes=3, max_batch=4096, large_mn=2048 * 1024, prec=RQ_MIXED,
+    def __init__(self, budget_bytes=120e9, lanes=3, max_batch=4096, large_mn=2048 * 1024, prec=RQ_FP32,
                  device=None, tiles=None):
-        """tiles: the batched kernel's tile policy (skinny_m, skinny_n) for every
+        """prec: RQ_FP32 (default: FP32 storage, FP32 sketch, 3xTF32 tensor-core
+        products, FP64 Householder scalars and norms), RQ_MIXED (the sketch from
+        bfloat16-rounded inputs) or RQ_FP64 (every request through rq_tuxv).
+        tiles: the batched kernel's tile policy (skinny_m, skinny_n) for every
         lane, e.g. from Handle.tune_batched on a representative batch; None
         keeps the library's default."""
         import torch
@@ -102,8 +107,8 @@ class Server:
     def submit(self, A, Omega, b, p, k):
         m, n = A.shape
         r = Request(A, Omega, b, p, k, arrival=time.perf_counter())
-        r.nbytes = footprint_bytes(m, n, k, b, p)
-        r.large = m * n > self.large_mn
+        r.nbytes = footprint_bytes(m, n, k, b, p, elem=8 if self.prec == RQ_FP64 else 4)
+        r.large = m * n > self.large_mn or self.prec == RQ_FP64
         if r.nbytes > self.budget:
             self.rejected += 1
             raise MemoryError("request larger than the server's HBM budget")
@@ -158,8 +163,7 @@ class Server:
                 with torch.cuda.stream(st):
                     if batch[0].large:
                         r = batch[0]
-                        prec = RQ_MIXED if self.prec == RQ_MIXED else RQ_FP32
-                        U2, X2, V2, _, info = h.tuxv(r.A, r.Omega, r.b, r.p, r.k, prec=prec, stream=st)
+                        U2, X2, V2, _, info = h.tuxv(r.A, r.Omega, r.b, r.p, r.k, prec=self.prec, stream=st)
                         r.out = (U2, X2, V2)
                         r.info = info
                     else:

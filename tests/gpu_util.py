@@ -71,3 +71,18 @@ def r_column_norms(F, k):
         tail = F[k:, j] if j >= k else np.zeros(0)
         out[j] = np.sqrt(np.sum(top * top) + np.sum(tail * tail))
     return out
+
+
+def fp64_oracle_error(a, om, b, k):
+    """Rank-k error ||A - U X V^T||_F / ||A||_F of the plain FP64 oracle (Alg. 6,
+    j_max = 1, FP64 sketch) on the FP64 input: the reference every
+    reduced-precision TUXV result is held to (within 1.05x, per problem)."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = O.tuxv(a, np.asarray(om, dtype=np.float64), b, k)
+    return float(np.linalg.norm(a - ref.U @ ref.X @ ref.V.T) / np.linalg.norm(a)), ref
+
+
+def rank_k_error(a, U, X, V):
+    """||A - U X V^T||_F / ||A||_F in FP64 against the FP64 input."""
+    a = np.asarray(a, dtype=np.float64)
+    return float(np.linalg.norm(a - U @ X @ V.T) / np.linalg.norm(a))

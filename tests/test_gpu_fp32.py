@@ -9,8 +9,13 @@ growth ||B^[0]|| / ||B^[J]|| of the sample's relative error under the update
 formula's cancellation: the products run as 3xTF32 on the tensor cores, whose
 FP32 accumulation carries about 10 u_32 = 6e-7 relative error, so a sample is
 accurate to about 6e-7 ||B^[0]|| / ||B^[J]|| and 1e-4 leaves a margin of 150;
-R within 1e-5 ||A||_F entry by entry when there is no near-tie; TUXV rank-k
-error within 1.05x the oracle's.
+R within 1e-5 ||A||_F entry by entry when there is no near-tie; after a
+near-tie the factorisation must still reveal rank as well as the oracle's:
+at every block boundary j whose trailing norm is at least 1e-3 ||A||_F (far
+above the FP32 residual), ||R(j:, j:)||_F within 1.05x that of the FP64
+oracle on the same input (the rank-j error of RQRCP, Sec. 3); TUXV rank-k
+error, in FP64 against the FP64 input, within 1.05x that of the plain FP64
+oracle on the FP64 input.
 """
 import numpy as np
 import pytest
@@ -18,7 +23,8 @@ import pytest
 import oracle as O
 from paper_2008_04447_gb300 import inputs as I
 
-from gpu_util import build_and_handle, factor_quality, first_near_tie, to_dev, to_host
+from gpu_util import (build_and_handle, factor_quality, first_near_tie, fp64_oracle_error, rank_k_error,
+                      to_dev, to_host)
 
 pytestmark = pytest.mark.gpu
 TIE = 1e-4
@@ -52,6 +58,19 @@ def test_rqrcp_fp32_matches_oracle(H, m, n, b, p):
     assert np.array_equal(jp[:upto], ref.jpvt[:upto])
     if tie is None:
         assert np.max(np.abs(np.triu(F[:k]) - np.triu(ref.F[:k]))) <= 1e-5 * np.linalg.norm(a)
+    # rank-revealing quality at every block boundary, before and after a near-tie
+    nrm = np.linalg.norm(a)
+    checked = 0
+    for j in range(b, k, b):
+        t_ref = np.linalg.norm(np.triu(ref.F[j:, j:]))
+        if t_ref < 1e-3 * nrm:
+            break
+        t_gpu = np.linalg.norm(np.triu(F[j:, j:]))
+        assert t_gpu <= 1.05 * t_ref, (j, t_gpu / t_ref)
+        checked += 1
+    assert checked >= 2
+    if tie is not None:
+        assert tie < checked * b + b    # the check reaches past the first near-tie
 
 
 @pytest.mark.parametrize("m,n,b", [(1000, 800, 64), (333, 555, 32)])
@@ -91,6 +110,6 @@ def test_trqrcp_and_tuxv_fp32(H, mode):
     U, X, V = to_host(U), to_host(X), to_host(V)
     assert np.allclose(U.T @ U, np.eye(k), atol=1e-5)
     assert np.allclose(V.T @ V, np.eye(k), atol=1e-5)
-    e_gpu = np.linalg.norm(a64 - U @ X @ V.T)
-    e_ref = np.linalg.norm(a64 - ref.U @ ref.X @ ref.V.T)
-    assert e_gpu <= 1.05 * e_ref
+    e_gpu = rank_k_error(a64, U, X, V)
+    e_64, _ = fp64_oracle_error(a64, I.omega(b + p, m, seed=22), b, k)
+    assert e_gpu <= 1.05 * e_64, e_gpu / e_64

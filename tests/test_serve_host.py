@@ -191,3 +191,21 @@ def test_an_allocation_failure_at_admission_fails_that_request(fakes, monkeypatc
     finish_all()
     srv.pump()
     assert good.wait(0) is not None and srv.used == 0 and srv.stats()["failed"] == 1
+
+
+def test_fp64_requests_all_go_to_the_single_problem_path(fakes):
+    """The batched kernel is FP32-only: in FP64 every request is launched alone
+    through rq_tuxv, and its footprint counts 8-byte elements."""
+    from paper_2008_04447_gb300 import RQ_FP64
+    srv = serve.Server(budget_bytes=1e9, lanes=3, device="cpu", prec=RQ_FP64)
+    rs = [srv.submit(*req(100, 80)) for _ in range(4)]
+    assert all(r.large for r in rs)
+    assert rs[0].nbytes == serve.footprint_bytes(100, 80, 8, 8, 4, elem=8)
+    srv.pump()
+    assert [e[0] for e in fakes] == ["tuxv", "tuxv", "tuxv"]
+    finish_all()
+    srv.pump()
+    finish_all()
+    srv.pump()
+    assert len(srv.completed) == 4 and srv.used == 0
+    assert all(e[0] == "tuxv" for e in fakes)
