@@ -161,15 +161,25 @@ int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p
  * device-wide synchronisation of cudaMalloc / cudaFree mid-request.  The
  * paper has no counterpart; this is a deployment variant.
  *
- * It allocates nothing: its scratch is a fixed device array of
+ * It runs rq_rqrcp's block loop over a fixed device array of
  * RQ_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
- * loads the library holds until the process exits.  A problem whose scratch
- * (about 8 B x (2 l n + 5 m b + b n + 3 b^2) for FP64, half the matrix terms
- * for FP32) exceeds it returns RQ_ETOOBIG before any launch.  All calls share
- * the array, so calls that overlap on the GPU race: serialise them.  The
- * first call on each device looks up the array's address with that device
- * current; make it before any stream capture.  prec is RQ_FP64 or RQ_FP32;
- * argument errors return -(index), counting prec as argument 1.
+ * loads the library holds until the process exits.  It keeps fewer split-K
+ * partial copies of the W^T product than a handle (none in FP64, four in
+ * FP32), so FP64 results equal rq_rqrcp's to rounding and FP32 results agree
+ * within the FP32 path's tolerances (the products may be cut into different
+ * inner-dimension chunks), not bit for bit.  Its scratch, with s the element
+ * size (8 FP64, 4 FP32), G the device's SM count and every term rounded up to
+ * 256 bytes, is
+ *   s (2 l n + b^2 + 2 ceil4(m) b + b n + 2 b m + c b n)
+ *   + 8 (3 b^2 + 2 G (l + 2) + 2 G (b + 1) + 4 b) + 4 (5 b + n) + 16
+ * bytes, c = 0 (FP64) or 4 (FP32), ceil4(m) = m rounded up to a multiple of
+ * 4: about 3.7 KB x n for FP64 at m = n, b = 64, p = 8 (n up to about 4400),
+ * 2.9 KB x n for FP32 (n up to about 5700).  A problem needing more returns RQ_ETOOBIG before any
+ * launch.  All calls share the array, so calls that overlap on the GPU race:
+ * serialise them.  Each call looks up the array's address with the current
+ * device; the first call on a device also loads the library there, so make
+ * it before any stream capture.  prec is RQ_FP64 or RQ_FP32; argument errors
+ * return -(index), counting prec as argument 1.
  */
 #define RQ_NOALLOC_SCRATCH_BYTES (16u << 20)
 int rq_rqrcp_noalloc(int prec, int m, int n, void* A, int lda, int b, int p, int k, const void* Omega,

@@ -142,4 +142,15 @@ cudaError_t finish_info(const Ctx& c, const TS* A, int lda, int k, int* info);
 template <typename TD, typename TS>
 cudaError_t convert(const Ctx& c, int rows, int cols, const TS* src, int lds, TD* dst, int ldd);
 
+// Blocked Householder QR (Alg. 4 with pivot, unpivoted without) over a
+// caller-provided workspace of factor_ws_bytes bytes; h may be NULL.  Shared by
+// rq_rqrcp / rq_qr / rq_rsrqrcp (the handle's workspace) and rq_rqrcp_noalloc
+// (a fixed device array), so both run the same block loop.
+template <typename TS>
+int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool pivot, int m, int n, TS* A, int lda,
+                  int b, int p, int k, const TS* Omega, int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st,
+                  const uint64_t* rs_seed, int splitk_copies);
+template <typename TS>
+size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies);
+
 }  // namespace rq

@@ -94,9 +94,9 @@ struct Phase {
   int phase, ev0;
   long long l0;
   Phase(rq_handle h_, cudaStream_t st_, int ph, double flops, double bytes)
-      : h(h_), st(st_), phase(ph), ev0(-1), l0(h_->launches) {
+      : h(h_), st(st_), phase(ph), ev0(-1), l0(h_ ? h_->launches : 0) {
     nvtxRangePushA(kPhaseNames[ph]);
-    if (!h->prof_on) return;
+    if (!h || !h->prof_on) return;
     ev0 = next_event(h);
     if (ev0 >= 0) cudaEventRecord(h->ev_pool[ev0], st);
     h->prof_flops[ph] += flops;
@@ -104,7 +104,7 @@ struct Phase {
   }
   ~Phase() {
     nvtxRangePop();
-    if (!h->prof_on || ev0 < 0) return;
+    if (!h || !h->prof_on || ev0 < 0) return;
     int ev1 = next_event(h);
     if (ev1 < 0) return;
     cudaEventRecord(h->ev_pool[ev1], st);
@@ -128,11 +128,14 @@ struct FactorWs {
 
 inline int pad4(int x) { return (x + 3) / 4 * 4; }
 
-// Split-K partials of the b x n W^T product: up to 16 partial copies.
-inline size_t splitk_bytes_for(int b, int n, size_t elem) { return 16 * (size_t)b * n * elem; }
+// Split-K partials of the b x n W^T product: up to `copies` partial copies.
+inline size_t splitk_bytes_for(int b, int n, size_t elem, int copies = 16) {
+  return (size_t)copies * b * n * elem;
+}
 
 template <typename TS>
-FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, bool resample = false) {
+FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, bool resample = false,
+                          int splitk_copies = 16) {
   Carver c(base);
   FactorWs<TS> w;
   w.bar = c.take<unsigned int>(4);
@@ -153,8 +156,8 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
   w.src = c.take<int>((size_t)n);
   w.cand = c.take<double>(sample_qrcp_scratch_doubles(l, num_sms));
   w.pscr = c.take<double>(panel_scratch_doubles(b, num_sms));
-  w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS));
-  w.splitk = c.take<char>(w.splitk_bytes);
+  w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS), splitk_copies);
+  w.splitk = splitk_copies > 0 ? c.take<char>(w.splitk_bytes) : nullptr;
   w.Om = resample ? c.take<TS>((size_t)l * m) : nullptr;
   w.bytes = align_up(c.off, 256);
   return w;
@@ -205,20 +208,22 @@ cudaError_t prod_nn(const Ctx& c, int M, int N, int K, TS alpha, const TS* A, in
   return gemm<TS>(c, false, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
-// Blocked Householder QR, pivoted by the sample (Alg. 4) or unpivoted.  With
-// rs_seed (repeated sampling, Sec. 3.4) Omega is drawn from (seed, 0) and each
-// block's sample is a fresh sketch of the trailing matrix by the draws of
-// (seed, J) instead of the update of Eq. (update1).
+}  // namespace
+
+// Blocked Householder QR, pivoted by the sample (Alg. 4) or unpivoted, over a
+// workspace `ws` of factor_ws_bytes bytes that the caller provides (the
+// handle's, or the fixed array of rq_rqrcp_noalloc).  With rs_seed (repeated
+// sampling, Sec. 3.4) Omega is drawn from (seed, 0) and each block's sample is
+// a fresh sketch of the trailing matrix by the draws of (seed, J) instead of
+// the update of Eq. (update1).  h may be NULL (no profiling, no message).
 template <typename TS>
-int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega,
-               int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st, const uint64_t* rs_seed = nullptr) {
+int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool pivot, int m, int n, TS* A, int lda,
+                  int b, int p, int k, const TS* Omega, int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st,
+                  const uint64_t* rs_seed, int splitk_copies) {
   const int l = pivot ? b + p : 1;
   const bool rs = pivot && rs_seed != nullptr;
-  FactorWs<TS> w = carve_factor<TS>(nullptr, m, n, b, l, h->num_sms, rs);
-  int rc = ensure_ws(h, w.bytes);
-  if (rc) return rc;
-  w = carve_factor<TS>(h->ws, m, n, b, l, h->num_sms, rs);
-  Ctx c{st, h->num_sms, &h->launches, w.err, w.bar, w.splitk, w.splitk_bytes};
+  FactorWs<TS> w = carve_factor<TS>(ws, m, n, b, l, num_sms, rs, splitk_copies);
+  Ctx c{st, num_sms, launches, w.err, w.bar, w.splitk, w.splitk_bytes};
   cudaError_t e = cudaMemsetAsync(w.bar, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
   if (jpvt && (e = iota(c, jpvt, n)) != cudaSuccess) return cuda_fail(h, e, "iota");
@@ -315,6 +320,30 @@ int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int
     if (e != cudaSuccess) return cuda_fail(h, e, "info");
   }
   return RQ_OK;
+}
+
+template <typename TS>
+size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies) {
+  return carve_factor<TS>(nullptr, m, n, b, pivot ? b + p : 1, num_sms, pivot && resample, splitk_copies).bytes;
+}
+
+template int factor_blocks<float>(rq_handle, void*, int, long long*, bool, int, int, float*, int, int, int, int,
+                                  const float*, int, float*, int*, int*, cudaStream_t, const uint64_t*, int);
+template int factor_blocks<double>(rq_handle, void*, int, long long*, bool, int, int, double*, int, int, int, int,
+                                   const double*, int, double*, int*, int*, cudaStream_t, const uint64_t*, int);
+template size_t factor_ws_bytes<float>(int, int, int, int, int, bool, bool, int);
+template size_t factor_ws_bytes<double>(int, int, int, int, int, bool, bool, int);
+
+namespace {
+
+// The handle's factorisation: grows the handle's workspace, then the block loop.
+template <typename TS>
+int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega,
+               int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st, const uint64_t* rs_seed = nullptr) {
+  int rc = ensure_ws(h, factor_ws_bytes<TS>(m, n, b, p, h->num_sms, pivot, rs_seed != nullptr, 16));
+  if (rc) return rc;
+  return factor_blocks<TS>(h, h->ws, h->num_sms, &h->launches, pivot, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt,
+                           info, st, rs_seed, 16);
 }
 
 // Workspace of truncated RQRCP (Alg. 5).

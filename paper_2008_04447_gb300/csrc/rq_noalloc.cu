@@ -7,15 +7,18 @@
 // cudaMalloc / cudaFree would add a device-wide synchronisation in the middle
 // of a request, and code that must not fail for lack of memory once it runs.
 //
+// The factorisation is the one rq_rqrcp runs (the same block loop,
+// factor_blocks), over the fixed array instead of a handle's workspace, with
+// fewer split-K partial copies (none in FP64) to keep the array modest.
+//
 // The scratch array is RQ_NOALLOC_SCRATCH_BYTES large and every GPU that
 // loads this library holds it until the process exits.  All calls share it:
 // calls that overlap on the GPU (different streams, or different host
-// threads) race on it and give wrong results; serialise them.  The first call
-// on a device looks up the array's device address (cudaGetSymbolAddress) with
-// that device current; make that first call before any stream capture.
-#include <cstdio>
-#include <mutex>
-
+// threads) race on it and give wrong results; serialise them.  Each call
+// looks up the array's device address (cudaGetSymbolAddress) with the
+// caller's device current, so the address is never stale after a device
+// reset; the first call on a device also loads the library's kernels there,
+// so make it before any stream capture.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -24,80 +27,25 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scratch[RQ_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-int g_sms[kMaxDevices] = {0};
 long long g_launches = 0;
 
-struct Carve {
-  char* base;
-  size_t off;
-  template <typename T>
-  T* take(size_t count) {
-    off = align_up(off, 256);
-    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-    off += count * sizeof(T);
-    return p;
-  }
-};
-
+// Split-K partial copies of the skinny W^T product: FP32 keeps four so the
+// tensor-core products can still cut long inner dimensions into chunks of at
+// most 1024; FP64 runs without.
 template <typename TS>
-struct Ws {
-  unsigned int* bar;
-  int* err;
-  TS *B0, *B1, *Ybuf, *YT, *Wt, *ptmp, *Tts;
-  double *S11, *Oh, *T, *cand, *pscr;
-  int *jtmp, *chg, *swaps, *src;
-  size_t bytes;
-};
+constexpr int kSplitCopies = sizeof(TS) == sizeof(float) ? 4 : 0;
 
-template <typename TS>
-Ws<TS> carve(void* base, int m, int n, int b, int l, int sms) {
-  Carve c{static_cast<char*>(base), 0};
-  Ws<TS> w;
-  w.bar = c.take<unsigned int>(4);
-  w.err = reinterpret_cast<int*>(w.bar + 2);
-  w.B0 = c.take<TS>((size_t)l * n);
-  w.B1 = c.take<TS>((size_t)l * n);
-  w.S11 = c.take<double>((size_t)b * b);
-  w.Oh = c.take<double>((size_t)b * b);
-  w.T = c.take<double>((size_t)b * b);
-  w.Tts = c.take<TS>((size_t)b * b);
-  w.Ybuf = c.take<TS>((size_t)m * b);
-  w.YT = c.take<TS>((size_t)m * b);
-  w.Wt = c.take<TS>((size_t)b * n);
-  w.ptmp = c.take<TS>((size_t)2 * b * m);
-  w.jtmp = c.take<int>((size_t)2 * b);
-  w.chg = c.take<int>((size_t)2 * b);
-  w.swaps = c.take<int>((size_t)b);
-  w.src = c.take<int>((size_t)n);
-  w.cand = c.take<double>(sample_qrcp_scratch_doubles(l, sms));
-  w.pscr = c.take<double>(panel_scratch_doubles(b, sms));
-  w.bytes = align_up(c.off, 256);
-  return w;
-}
-
-// Device address of the static array and SM count of the current device,
-// looked up once per device (the set-up the file header describes).
+// Device address of the static array and SM count of the current device.
 int setup(void** addr, int* sms) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RQ_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return RQ_ECUDA;
-    }
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RQ_ECUDA;
-    g_addr[dev] = p;
-    g_sms[dev] = n;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RQ_ECUDA;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return RQ_ECUDA;
   }
-  *addr = g_addr[dev];
-  *sms = g_sms[dev];
+  if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RQ_ECUDA;
+  *addr = p;
   return RQ_OK;
 }
 
@@ -108,51 +56,11 @@ int run(int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega, int 
   int sms = 0;
   int rc = setup(&base, &sms);
   if (rc) return rc;
-  const int l = b + p;
-  Ws<TS> w = carve<TS>(nullptr, m, n, b, l, sms);
-  if (w.bytes > (size_t)RQ_NOALLOC_SCRATCH_BYTES) return RQ_ETOOBIG;
-  w = carve<TS>(base, m, n, b, l, sms);
-  Ctx c{st, sms, &g_launches, w.err, w.bar};
-  // the array keeps the previous call's contents: the barrier words must start at zero
-  if (cudaMemsetAsync(w.bar, 0, 16, st) != cudaSuccess) return RQ_ECUDA;
-  if (iota(c, jpvt, n) != cudaSuccess) return RQ_ECUDA;
-  TS* Bc = w.B0;
-  TS* Bn = w.B1;
-  if (gemm<TS>(c, false, false, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l) != cudaSuccess) return RQ_ECUDA;
-  for (int j0 = 0; j0 < k; j0 += b) {
-    const int bj = (k - j0) < b ? (k - j0) : b;
-    const int nt = n - j0, mt = m - j0, n2 = nt - bj;
-    TS* Aj = A + j0 + (size_t)j0 * lda;
-    cudaError_t e = sample_qrcp<TS>(c, Bc, l, l, nt, bj, Bn, l, w.S11, b, w.swaps, w.src, w.chg, w.cand);
-    if (e == cudaSuccess)
-      e = permute_columns<TS>(c, A + (size_t)j0 * lda, lda, m, bj, w.chg, w.src, jpvt + j0, w.ptmp, w.jtmp);
-    if (e == cudaSuccess) e = panel_qr<TS>(c, Aj, lda, mt, bj, tau + j0, w.Ybuf, mt, w.T, b, w.pscr);
-    if (e == cudaSuccess && n2 > 0) {
-      TS* A2 = A + j0 + (size_t)(j0 + bj) * lda;
-      const TS* Tm = reinterpret_cast<const TS*>(w.T);
-      if (sizeof(TS) != sizeof(double)) {
-        e = convert<TS, double>(c, bj, bj, w.T, b, w.Tts, b);
-        Tm = w.Tts;
-      }
-      if (e == cudaSuccess) e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, mt, Tm, b, TS(0), w.YT, mt);
-      if (e == cudaSuccess) e = gemm<TS>(c, true, false, bj, n2, mt, TS(1), w.YT, mt, A2, lda, TS(0), w.Wt, b);
-      if (e == cudaSuccess)
-        e = gemm<TS>(c, false, false, mt, n2, bj, TS(-1), w.Ybuf, mt, w.Wt, b, TS(1), A2, lda);
-      if (e == cudaSuccess && j0 + bj < k) {
-        e = omegahat11<TS>(c, w.S11, b, Aj, lda, bj, w.Oh, b);
-        if (e == cudaSuccess) e = sample_update<TS>(c, bj, n2, w.Oh, b, A2, lda, Bn, l);
-      }
-    }
-    if (e != cudaSuccess) {
-      return (e == cudaErrorInvalidConfiguration || e == cudaErrorCooperativeLaunchTooLarge) ? RQ_ENOTIMPL
-                                                                                              : RQ_ECUDA;
-    }
-    TS* t = Bc;
-    Bc = Bn;
-    Bn = t;
-  }
-  if (finish_info<TS>(c, A, lda, k, info) != cudaSuccess) return RQ_ECUDA;
-  return RQ_OK;
+  if (factor_ws_bytes<TS>(m, n, b, p, sms, true, false, kSplitCopies<TS>) > (size_t)RQ_NOALLOC_SCRATCH_BYTES)
+    return RQ_ETOOBIG;
+  // factor_blocks clears the barrier words first: the array keeps the previous call's contents
+  return factor_blocks<TS>(nullptr, base, sms, &g_launches, true, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info,
+                           st, nullptr, kSplitCopies<TS>);
 }
 
 }  // namespace
