@@ -357,6 +357,33 @@ int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, cons
                  int ldc, int* info, rq_stream stream);
 
 /*
+ * rq_gemm_f64 -- C = A B in FP64 on the bfloat16 tensor cores: the product the
+ * FP64 factorisations' block reflector updates use (Alg. 4's trailing update
+ * W^T = (Y T)^T A2, A2 -= Y W^T), for other FP64 matrices.
+ *   A  M x K (lda >= M), B  K x N (ldb >= K), C  M x N (ldc >= M, out):
+ *      FP64, column-major, device arrays owned by the caller; C must not
+ *      overlap A or B (an overlap returns -9).
+ *   info  nullable device int32 (out): 0, or RQ_ETIMEOUT if a bounded wait of
+ *         the tensor-core kernel ran out.
+ * Each row of A and each column of B is scaled by a power of two from its
+ * largest entry and cut into eight signed 7-bit slices (exact in bfloat16);
+ * the 36 slice pairs whose weights reach 2^-63 of the leading pair are
+ * multiplied on the tensor cores, summed per weight in FP32 over at most 128
+ * steps of K (exact: every partial sum stays below 2^24), gathered in int64
+ * and returned to FP64 with one rounding.  The error is about that of an FP64
+ * GEMM: below (3 K 2^-53 + 2^-52) 2^(ea_i + eb_j) per entry, with 2^ea_i and
+ * 2^eb_j the powers of two just above the largest magnitude of row i of A and
+ * column j of B (entries of 2^-1000 or less relative to their row's largest
+ * lose accuracy to underflow).  The handle's workspace holds the slices:
+ * 16 (ceil128(M) + ceil64(N)) ceil64(K) bytes, plus FP64 split-K partials.
+ * Errors: -(argument index) for M, N or K < 1, a NULL array or a short
+ * leading dimension (h is argument 1); RQ_ENOTIMPL without a tensor-map
+ * encoder in the driver.  Asynchronous on stream.
+ */
+int rq_gemm_f64(rq_handle h, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                int ldc, int* info, rq_stream stream);
+
+/*
  * Tile policy of rq_tuxv_batched's block-level FP32 products.  A product with
  * M output rows and N output columns runs on 32 x 128 tiles when
  * M <= skinny_m, else on 128 x 32 tiles when N <= skinny_n, else on 64 x 64

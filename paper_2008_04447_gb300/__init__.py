@@ -16,7 +16,7 @@ from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_
                    rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp,
                    rq_tuxv, rq_tuxv_batched, rq_tuxv_iter, rq_latent_cdf, rq_padding,
                    rq_workspace_size, rq_set_batch_tiles, rq_get_batch_tiles, rq_tiles_search, rq_tune_batched,
-                   rq_gemm_bf16, rq_selftest_wait_timeout)
+                   rq_gemm_bf16, rq_gemm_f64, rq_selftest_wait_timeout)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
 
@@ -271,6 +271,20 @@ class Handle:
         info = torch.zeros(1, dtype=torch.int32, device=A.device)
         rc = rq_gemm_bf16(self.h, M, N, K, A, _ld(A), B, _ld(B), C, _ld(C), info, stream)
         self._check(rc, "rq_gemm_bf16")
+        return C, info
+
+    def gemm_f64(self, A, B, out=None, stream=None):
+        """C = A B of column-major FP64 device matrices on the bfloat16 tensor
+        cores (sliced operands, FP64 accuracy).  Returns (C, info)."""
+        import torch
+        M, K = A.shape
+        K2, N = B.shape
+        if K2 != K:
+            raise ValueError(f"inner dimensions differ: {K} and {K2}")
+        C = torch.empty((N, M), dtype=torch.float64, device=A.device).t() if out is None else out
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+        rc = rq_gemm_f64(self.h, M, N, K, A, _ld(A), B, _ld(B), C, _ld(C), info, stream)
+        self._check(rc, "rq_gemm_f64")
         return C, info
 
     def gaussian(self, l, m, seed, substream=0, dtype=None, out=None, stream=None):

@@ -59,6 +59,7 @@ _SIGS = {
     "rq_tuxv_iter": ([_P, _I, _I, _I, _P, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P], _I),
     "rq_tuxv_batched": ([_P, _I, _I, _P, _I, _I, _I, _I, _I, _P], _I),
     "rq_gemm_bf16": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P], _I),
+    "rq_gemm_f64": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P], _I),
     "rq_set_batch_tiles": ([_P, ctypes.POINTER(rq_batch_tiles)], _I),
     "rq_get_batch_tiles": ([_P, ctypes.POINTER(rq_batch_tiles)], _I),
     "rq_tiles_search": ([rq_tiles_measure, _P, ctypes.POINTER(rq_batch_tiles), _I, ctypes.POINTER(rq_batch_tiles),
@@ -195,6 +196,10 @@ def rq_tuxv_batched(h, prec, count, problems, max_m, max_n, max_k, max_b, max_p,
 
 def rq_gemm_bf16(h, M, N, K, A, lda, B, ldb, C, ldc, info=None, stream=None):
     return load().rq_gemm_bf16(h, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, _ptr(info), _stream(stream))
+
+
+def rq_gemm_f64(h, M, N, K, A, lda, B, ldb, C, ldc, info=None, stream=None):
+    return load().rq_gemm_f64(h, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, _ptr(info), _stream(stream))
 
 
 def rq_set_batch_tiles(h, skinny_m, skinny_n):

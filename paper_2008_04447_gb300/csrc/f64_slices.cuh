@@ -8,14 +8,16 @@
 //   2^(56 - e), e the exponent with max |x| < 2^e over that row (column), and
 //   each entry truncated to the integer X = trunc(|x| 2^(56 - e)) < 2^56,
 //   from the FP64 bit pattern alone (no FP64 arithmetic).
-// * X is cut into seven 8-bit slices, most significant first, each carrying
-//   the sign of x: X = sum_{i=1..7} |s_i| 2^(8 (7 - i)), |s_i| <= 255 (exact
+// * X is cut into eight 7-bit slices, most significant first, each carrying
+//   the sign of x: X = sum_{i=1..8} |s_i| 2^(7 (8 - i)), |s_i| <= 127 (exact
 //   in bfloat16).
-// * A product of two slices is an integer below 2^16, so an FP32 sum of up to
-//   256 of them is exact.  The pairs (i, j) with i + j = L (L = 2..8; pairs
-//   with i + j > 8 are dropped: at most about 2^-53 2^(ea + eb) per term)
-//   form level L:
-//     sum_k a_k b_k ~= 2^(ea + eb - 112) sum_L P_L 2^(112 - 8 L).
+// * A product of two slices is an integer of magnitude at most 127^2 < 2^14.
+//   The pairs (i, j) with i + j = L (L = 2..9, at most eight pairs a level;
+//   pairs with i + j > 9 are dropped: at most about 2^-53 2^(ea + eb) per
+//   term) form level L:
+//     sum_k a_k b_k ~= 2^(ea + eb - 112) sum_L P_L 2^(112 - 7 L),
+//   and a level's sum over up to 128 consecutive k stays below
+//   8 x 128 x 127^2 < 2^24, so an FP32 accumulator holds it exactly.
 // * Each level's exact FP32 partial is drained into one int64 kept in units
 //   of 2^u, u = 50 + ceil(log2 K): the sum of all terms' magnitudes is below
 //   K 2^112, so no partial sum can leave the int64 range.  Levels whose unit
@@ -39,9 +41,10 @@
 
 namespace rq {
 
-constexpr int kF64Slices = 7;                 // slices per operand entry
+constexpr int kF64Slices = 8;                 // slices per operand entry
+constexpr int kF64SliceBits = 7;              // bits per slice (|s| <= 127)
 constexpr int kF64Levels = kF64Slices;        // levels L = 2 .. kF64Slices + 1
-constexpr int kF64ChunkK = 32;                // K steps per exact FP32 partial (7 pairs x 32 x 255^2 < 2^24)
+constexpr int kF64ChunkK = 128;               // K steps per exact FP32 partial (8 pairs x 128 x 127^2 < 2^24)
 
 RQ_HD uint64_t f64_bits(double x) {
 #ifdef __CUDA_ARCH__
@@ -90,13 +93,13 @@ RQ_HD uint64_t f64_scaled_int(double x, int e) {
   return M >> (-sh);
 }
 
-// The seven signed slices of x under the exponent e, most significant first.
+// The eight signed slices of x under the exponent e, most significant first.
 RQ_HD void f64_slices(double x, int e, int s[kF64Slices]) {
   const uint64_t X = f64_scaled_int(x, e);
   const bool neg = (f64_bits(x) >> 63) != 0;
 #pragma unroll
   for (int i = 0; i < kF64Slices; ++i) {
-    const int v = static_cast<int>((X >> (8 * (kF64Slices - 1 - i))) & 0xFFu);
+    const int v = static_cast<int>((X >> (kF64SliceBits * (kF64Slices - 1 - i))) & 0x7Fu);
     s[i] = neg ? -v : v;
   }
 }
@@ -108,11 +111,11 @@ RQ_HD int f64_acc_unit(int K) {
   return 50 + c;
 }
 
-// acc += P 2^(112 - 8 L - u): P, level L's exact partial (an integer held in
+// acc += P 2^(112 - 7 L - u): P, level L's exact partial (an integer held in
 // FP32, |P| < 2^24); rounded to nearest when the level's unit is below 2^u.
 RQ_HD void f64_add_level(int64_t& acc, float P, int L, int u) {
   const int64_t p = static_cast<int64_t>(P);
-  const int sh = 112 - 8 * L - u;
+  const int sh = 112 - kF64SliceBits * L - u;
   if (sh >= 0)
     acc += p * (static_cast<int64_t>(1) << sh);
   else if (sh > -40)                             // |p| < 2^24: a shift of 40 or more leaves 0

@@ -1,0 +1,404 @@
+// FP64 matrix products on the bfloat16 tensor cores, to FP64 accuracy.
+//
+// GB300's FP64 pipe issues about two FMAs per clock per SM (1.26 TFLOP/s),
+// while its tensor cores multiply bfloat16 at 2.25 PFLOP/s.  The block
+// reflector products of the FP64 factorisation (Alg. 4) therefore run here as
+// an Ozaki-style error-free split (Ozaki, Ogita, Oishi and Rump, 2012), with
+// the integer steps of f64_slices.cuh:
+//
+//   D = A B^T, A M x K and B N x K (row r of an operand is its K entries).
+//   Each operand row r is scaled by 2^(56 - e_r) (e_r from its largest entry)
+//   and cut into eight signed 7-bit slices, stored as bfloat16 "planes"
+//   (plane s holds slice s of every entry, K-major, [8][rows][Kp]).  For every
+//   slice pair (i, j) with i + j <= 9 (36 pairs) the tensor cores add the
+//   exact products A_i B_j^T into one FP32 TMEM accumulator per level
+//   L = i + j (8 levels x 64 columns = all 512 TMEM columns).  After every
+//   128 steps of K (a level's sum is then below 2^24: exact in FP32) the
+//   levels are drained into int64 registers in units of 2^u, and at the end
+//   the int64 sums return to FP64 with one rounding and the two exponents.
+//
+// Kernel: one CTA per 128 x 64 tile of D (and K range, for split-K).
+//   warp 0     : TMA producer (eight A planes of 128 x 64 and eight B planes of
+//                64 x 64 per 64-step K stage: 192 KB, one stage)
+//   warp 1     : TMEM allocation and the single-thread tcgen05.mma issue
+//   warps 2..9 : drain TMEM into int64 accumulators (warp w reads TMEM lane
+//                quarter w % 4, columns 32 ((w - 2) / 4) ..), then the FP64
+//                epilogue C = alpha D + beta C
+// All waits are bounded: on a timeout the kernel records RQ_ETIMEOUT, lets its
+// copies land, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "common.cuh"
+#include "f64_slices.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace rq {
+namespace {
+using namespace tc;
+
+constexpr int OZ_BM = 128;                       // tile rows = TMEM lanes
+constexpr int OZ_BN = 64;                        // tile columns
+constexpr int OZ_BK = 64;                        // K per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int OZ_S = kF64Slices;                 // 8 slices
+constexpr int OZ_THREADS = 320;
+constexpr uint32_t OZ_ABYTES = OZ_BM * OZ_BK * 2;             // one A plane tile: 16 KB
+constexpr uint32_t OZ_BBYTES = OZ_BN * OZ_BK * 2;             // one B plane tile: 8 KB
+constexpr uint32_t OZ_STAGE = OZ_S * (OZ_ABYTES + OZ_BBYTES); // 192 KB
+constexpr uint32_t OZ_TMEM_COLS = OZ_S * OZ_BN;               // 512
+constexpr int OZ_STAGES_PER_CHUNK = kF64ChunkK / OZ_BK;       // 2 stages between drains
+
+static_assert(OZ_TMEM_COLS == 512, "one 64-column accumulator per level fills TMEM");
+
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = 64.
+__host__ __device__ constexpr uint32_t bf16_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 2^e as an FP64 value (e in the normal range).
+__device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+struct OzArgs {
+  int M, N, K;              // D = A B^T: A M x K, B N x K
+  int Mp, Np;               // plane row counts (the row offset of plane s is s Mp, s Np)
+  int kchunk;               // K range of blockIdx.z (a multiple of OZ_BK)
+  int u;                    // accumulator unit exponent, >= f64_acc_unit(K)
+  const int* ea;            // M row exponents of A
+  const int* eb;            // N row exponents of B
+  double alpha, beta;
+  double* C;                // element (i, j) at C[i rs + j cs] (+ z czs for split-K partials)
+  long long rs, cs;
+  size_t czs;
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int kbeg = blockIdx.z * a.kchunk;
+  const int kend = min(a.K, kbeg + a.kchunk);
+  const int nk = (kend - kbeg + OZ_BK - 1) / OZ_BK;
+  const int nchunks = (nk + OZ_STAGES_PER_CHUNK - 1) / OZ_STAGES_PER_CHUNK;
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t full = bar0, empty = bar0 + 8, dfull = bar0 + 16, dempty = bar0 + 24;
+  unsigned char* sA = sm;                          // plane s at sA + s OZ_ABYTES
+  unsigned char* sB = sm + OZ_S * OZ_ABYTES;       // plane s at sB + s OZ_BBYTES
+
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    mbar_init(dfull, 1);
+    mbar_init(dempty, 256);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        if (!mbar_wait(empty, (it & 1) ^ 1, a.err)) break;
+        mbar_expect_tx(full, OZ_STAGE);
+        const int k = kbeg + it * OZ_BK;
+#pragma unroll 1
+        for (int s = 0; s < OZ_S; ++s) {
+          tma_load_2d(smem_u32(sA + s * OZ_ABYTES), &mapA, k, s * a.Mp + m0, full);
+          tma_load_2d(smem_u32(sB + s * OZ_BBYTES), &mapB, k, s * a.Np + n0, full);
+        }
+        issued = it + 1;
+      }
+      // let the last copy land before the CTA may exit
+      if (issued > 0) mbar_wait(full, (issued - 1) & 1, a.err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = bf16_idesc();
+      for (int it = 0; it < nk; ++it) {
+        const int st = it % OZ_STAGES_PER_CHUNK;
+        const int c = it / OZ_STAGES_PER_CHUNK;
+        // the first stage of a chunk overwrites the levels: the previous chunk must be drained
+        if (st == 0 && c > 0 && !mbar_wait(dempty, (c - 1) & 1, a.err)) break;
+        if (!mbar_wait(full, it & 1, a.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int i = 0; i < OZ_S; ++i) {
+          const uint32_t ai = smem_u32(sA + i * OZ_ABYTES);
+#pragma unroll 1
+          for (int j = 0; j + i < OZ_S; ++j) {
+            const uint32_t bj = smem_u32(sB + j * OZ_BBYTES);
+            const uint32_t d = tmem + (uint32_t)((i + j) * OZ_BN);
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+              // the pair (0, L) opens level L in each chunk
+              const uint32_t acc = (st == 0 && i == 0 && kk == 0) ? 0u : 1u;
+              mma_bf16(d, sw128_desc(ai + kk * 32), sw128_desc(bj + kk * 32), idesc, acc);
+            }
+          }
+        }
+        mma_commit(empty);
+        if (st == OZ_STAGES_PER_CHUNK - 1 || it == nk - 1) mma_commit(dfull);
+      }
+    }
+  } else {
+    // warps 2..9: drain every chunk into int64, then the FP64 epilogue
+    const int q = warp & 3;           // TMEM lane quarter this warp may read
+    const int h = (warp - 2) >> 2;    // column half
+    const int row = m0 + q * 32 + lane;
+    int64_t acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      if (!mbar_wait(dfull, c & 1, a.err)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int L = 0; L < OZ_S; ++L) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(L * OZ_BN + 32 * h);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f64_add_level(acc[j], __uint_as_float(r[j]), L + 2, a.u);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(dempty);
+    }
+    if (ok && row < a.M) {
+      const int er = a.ea[row] + a.u - 112;
+      double* C = a.C + blockIdx.z * a.czs;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + 32 * h + j;
+        if (col < a.N) {
+          const int ex = er + a.eb[col];
+          double v = static_cast<double>(acc[j]);
+          v = (ex >= -1022 && ex <= 1023) ? v * pow2i(ex) : ldexp(v, ex);
+          double* out = C + (long long)row * a.rs + (long long)col * a.cs;
+          *out = a.beta != 0.0 ? fma(a.alpha, v, a.beta * *out) : a.alpha * v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+// bfloat16 bits of a small integer (|v| <= 127: exact, the low 16 bits of the FP32 value are zero).
+__device__ __forceinline__ uint32_t bf16_bits_of(int v) { return __float_as_uint(static_cast<float>(v)) >> 16; }
+
+// Operand rows are source COLUMNS: row r's K entries are src[k + r ld] (contiguous).
+// One warp per row: the largest magnitude (compared as bit patterns), its exponent,
+// then the eight planes; rows r >= R and entries k >= K are zero.
+__global__ void slice_cols_kernel(int R, int K, const double* __restrict__ src, long long ld, int Rp, int Kp,
+                                  uint16_t* __restrict__ planes, int* __restrict__ e) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= Rp) return;
+  const double* col = src + (long long)r * ld;
+  unsigned long long mx = 0;
+  if (r < R)
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(col[k])) & 0x7fffffffffffffffull;
+      mx = b > mx ? b : mx;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  const int ex = f64_scale_exponent(__longlong_as_double(static_cast<long long>(mx)));
+  if (lane == 0) e[r] = ex;
+  const size_t pstride = (size_t)Rp * Kp;
+  uint16_t* out = planes + (size_t)r * Kp;
+  for (int k = lane; k < Kp; k += 32) {
+    const double x = (r < R && k < K) ? col[k] : 0.0;
+    int s[OZ_S];
+    f64_slices(x, ex, s);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(bf16_bits_of(s[i]));
+  }
+}
+
+// Operand rows are source ROWS: row r's K entries are src[r + k ld] (one thread
+// per row; a warp reads 32 consecutive rows of a column at once).
+__global__ void slice_rows_kernel(int R, int K, const double* __restrict__ src, long long ld, int Rp, int Kp,
+                                  uint16_t* __restrict__ planes, int* __restrict__ e) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= Rp) return;
+  unsigned long long mx = 0;
+  if (r < R)
+    for (int k = 0; k < K; ++k) {
+      const unsigned long long b =
+          static_cast<unsigned long long>(__double_as_longlong(src[r + (long long)k * ld])) & 0x7fffffffffffffffull;
+      mx = b > mx ? b : mx;
+    }
+  const int ex = f64_scale_exponent(__longlong_as_double(static_cast<long long>(mx)));
+  e[r] = ex;
+  const size_t pstride = (size_t)Rp * Kp;
+  uint16_t* out = planes + (size_t)r * Kp;
+  for (int k0 = 0; k0 < Kp; k0 += 8) {
+    uint32_t w[OZ_S][4];
+#pragma unroll
+    for (int t = 0; t < 8; t += 2) {
+      int s0[OZ_S], s1[OZ_S];
+      const int k = k0 + t;
+      f64_slices((r < R && k < K) ? src[r + (long long)k * ld] : 0.0, ex, s0);
+      f64_slices((r < R && k + 1 < K) ? src[r + (long long)(k + 1) * ld] : 0.0, ex, s1);
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) w[i][t / 2] = bf16_bits_of(s0[i]) | (bf16_bits_of(s1[i]) << 16);
+    }
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i)
+      *reinterpret_cast<uint4*>(out + i * pstride + k0) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+  }
+}
+
+// C = alpha sum_z P_z + beta C over the split-K partials (P_z compact, M x N
+// column-major), C element (i, j) at C[i rs + j cs].
+__global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__ P, size_t pzs, double alpha,
+                                 double beta, double* C, long long rs, long long cs) {
+  const size_t total = (size_t)M * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % M), j = (int)(t / M);
+    double s = 0.0;
+    for (int z = 0; z < S; ++z) s += P[z * pzs + t];
+    double* out = C + (long long)i * rs + (long long)j * cs;
+    *out = beta != 0.0 ? fma(alpha, s, beta * *out) : alpha * s;
+  }
+}
+
+// 2-D map over the planes [8][rows_per_plane][Kp] bf16: box {64, box_rows}, 128-byte swizzle.
+bool make_plane_map(CUtensorMap* map, const uint16_t* base, int Kp, int rows_total, int box_rows) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows_total};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t oz_smem() { return OZ_STAGE + 1024; }
+
+}  // namespace
+
+int oz_rows_pad(int rows, bool a_side) { return a_side ? (rows + OZ_BM - 1) / OZ_BM * OZ_BM : (rows + OZ_BN - 1) / OZ_BN * OZ_BN; }
+int oz_k_pad(int K) { return (K + OZ_BK - 1) / OZ_BK * OZ_BK; }
+size_t oz_plane_bytes(int rows_pad, int k_pad) { return (size_t)OZ_S * rows_pad * k_pad * sizeof(uint16_t); }
+bool oz_supported() { return encoder() != nullptr; }
+
+cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const double* src, long long ld, int Rp, int Kp,
+                     uint16_t* planes, int* e) {
+  if (Rp <= 0) return cudaSuccess;
+  if (k_along_columns) {
+    slice_cols_kernel<<<(Rp + 7) / 8, 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
+  } else {
+    slice_rows_kernel<<<(Rp + 127) / 128, 128, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
+  }
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int Mp, const int* ea, const uint16_t* Bp,
+                    int Np, const int* eb, int Kp, double alpha, double beta, double* C, long long rs, long long cs) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  CUtensorMap ma, mb;
+  if (!make_plane_map(&ma, Ap, Kp, OZ_S * Mp, OZ_BM) || !make_plane_map(&mb, Bp, Kp, OZ_S * Np, OZ_BN))
+    return cudaErrorInvalidValue;
+  const int tiles = (Mp / OZ_BM) * (Np / OZ_BN);
+  // split K when the tiles do not fill the GPU (chunks of whole drains, partials in FP64)
+  int S = 1;
+  if (c.splitk && K > 2 * kF64ChunkK && tiles < c.num_sms) {
+    S = (c.num_sms + tiles - 1) / tiles;
+    const int maxS = (K + kF64ChunkK - 1) / kF64ChunkK;
+    if (S > maxS) S = maxS;
+    const size_t cap = c.splitk_bytes / (sizeof(double) * (size_t)M * N);
+    if ((size_t)S > cap) S = (int)cap;
+    if (S < 2) S = 1;
+  }
+  int kchunk = Kp;
+  if (S > 1) {
+    kchunk = ((K + S - 1) / S + kF64ChunkK - 1) / kF64ChunkK * kF64ChunkK;
+    S = (K + kchunk - 1) / kchunk;
+  }
+  OzArgs args;
+  args.M = M;
+  args.N = N;
+  args.K = K;
+  args.Mp = Mp;
+  args.Np = Np;
+  args.kchunk = kchunk;
+  args.u = f64_acc_unit(K);
+  args.ea = ea;
+  args.eb = eb;
+  args.err = c.err;
+  if (S == 1) {
+    args.alpha = alpha;
+    args.beta = beta;
+    args.C = C;
+    args.rs = rs;
+    args.cs = cs;
+    args.czs = 0;
+  } else {
+    args.alpha = 1.0;
+    args.beta = 0.0;
+    args.C = static_cast<double*>(c.splitk);
+    args.rs = 1;
+    args.cs = M;
+    args.czs = (size_t)M * N;
+  }
+  const size_t smem = oz_smem();
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(Mp / OZ_BM, Np / OZ_BN, S);
+  oz_gemm_kernel<<<grid, OZ_THREADS, smem, c.stream>>>(ma, mb, args);
+  ++*c.launches;
+  e = cudaGetLastError();
+  if (e != cudaSuccess || S == 1) return e;
+  const size_t total = (size_t)M * N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 8 * c.num_sms) blocks = 8 * c.num_sms;
+  oz_reduce_kernel<<<blocks, 256, 0, c.stream>>>(M, N, S, static_cast<const double*>(c.splitk), total, alpha, beta, C,
+                                                 rs, cs);
+  ++*c.launches;
+  return cudaGetLastError();
+}
+
+}  // namespace rq

@@ -142,15 +142,33 @@ cudaError_t finish_info(const Ctx& c, const TS* A, int lda, int k, int* info);
 template <typename TD, typename TS>
 cudaError_t convert(const Ctx& c, int rows, int cols, const TS* src, int lds, TD* dst, int ldd);
 
+// FP64 products on the bfloat16 tensor cores (f64_tc.cu).  An operand is held
+// as eight bfloat16 slice planes [8][rows_pad][k_pad] plus one exponent per
+// row; oz_slice makes them from an FP64 matrix whose operand rows are its
+// columns (k_along_columns: row r's entries at src[k + r ld]) or its rows
+// (src[r + k ld]).  oz_gemm: C = alpha A B^T + beta C, C element (i, j) at
+// C[i rs + j cs]; A M x K (rows padded to 128), B N x K (rows padded to 64).
+int oz_rows_pad(int rows, bool a_side);
+int oz_k_pad(int K);
+size_t oz_plane_bytes(int rows_pad, int k_pad);
+bool oz_supported();
+cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const double* src, long long ld, int Rp, int Kp,
+                     uint16_t* planes, int* e);
+cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int Mp, const int* ea, const uint16_t* Bp,
+                    int Np, const int* eb, int Kp, double alpha, double beta, double* C, long long rs, long long cs);
+
 // Blocked Householder QR (Alg. 4 with pivot, unpivoted without) over a
 // caller-provided workspace of factor_ws_bytes bytes; h may be NULL.  Shared by
 // rq_rqrcp / rq_qr / rq_rsrqrcp (the handle's workspace) and rq_rqrcp_noalloc
 // (a fixed device array), so both run the same block loop.
+// f64tc (FP64 only): 0 block reflector products on the FP64 pipe, 1 the update
+// A2 -= Y W^T on the bfloat16 tensor cores (oz_gemm), 2 also W^T = (Y T)^T A2.
 template <typename TS>
 int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool pivot, int m, int n, TS* A, int lda,
                   int b, int p, int k, const TS* Omega, int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st,
-                  const uint64_t* rs_seed, int splitk_copies);
+                  const uint64_t* rs_seed, int splitk_copies, int f64tc);
 template <typename TS>
-size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies);
+size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies,
+                       int f64tc);
 
 }  // namespace rq

@@ -6,6 +6,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -30,6 +31,9 @@ struct rq_handle_s {
   char last_error[256];
   // tile policy of the batched kernel's block GEMMs (rq_batch_tiles)
   int tile_m, tile_n;
+  // FP64 block reflector products on the bfloat16 tensor cores: 0 off (FP64
+  // pipe), 1 the update A2 -= Y W^T only, 2 also W^T = (Y T)^T A2
+  int f64_tc;
   // per-phase timing (rq_profile_enable)
   bool prof_on;
   std::vector<cudaEvent_t> ev_pool;
@@ -112,6 +116,31 @@ struct Phase {
   }
 };
 
+// Scratch of one FP64 tensor-core product: barrier / error words, the two
+// operands' slice planes and exponents, and FP64 split-K partials.
+struct OzWs {
+  unsigned int* bar;
+  int* err;
+  uint16_t *Ap, *Bp;
+  int *ea, *eb;
+  char* split;
+  size_t split_bytes;
+};
+
+OzWs carve_oz(Carver& cv, int Mp, int Np, int Kp, size_t mn) {
+  OzWs z;
+  z.bar = cv.take<unsigned int>(4);
+  z.err = reinterpret_cast<int*>(z.bar + 2);
+  z.Ap = cv.take<uint16_t>(oz_plane_bytes(Mp, Kp) / 2);
+  z.Bp = cv.take<uint16_t>(oz_plane_bytes(Np, Kp) / 2);
+  z.ea = cv.take<int>(Mp);
+  z.eb = cv.take<int>(Np);
+  const int chunks = (Kp + 127) / 128;
+  z.split_bytes = (size_t)(chunks < 16 ? chunks : 16) * sizeof(double) * mn;
+  z.split = cv.take<char>(z.split_bytes);
+  return z;
+}
+
 // Workspace of the full / unpivoted factorisation (RQRCP and QR).
 template <typename TS>
 struct FactorWs {
@@ -123,6 +152,11 @@ struct FactorWs {
   int *jtmp, *chg, *swaps, *src;
   char* splitk;
   size_t splitk_bytes;
+  // slice planes and exponents of the FP64 tensor-core products (FP64 only):
+  // 1 = W^T = (Y T)^T A2 (A2's columns, Y T's columns), 2 = A2 -= Y W^T (Y's
+  // rows, W^T's columns)
+  uint16_t *Ap1, *Bp1, *Ap2, *Bp2;
+  int *ea1, *eb1, *ea2, *eb2;
   size_t bytes;
 };
 
@@ -135,7 +169,7 @@ inline size_t splitk_bytes_for(int b, int n, size_t elem, int copies = 16) {
 
 template <typename TS>
 FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, bool resample = false,
-                          int splitk_copies = 16) {
+                          int splitk_copies = 16, int f64tc = 0) {
   Carver c(base);
   FactorWs<TS> w;
   w.bar = c.take<unsigned int>(4);
@@ -159,6 +193,22 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
   w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS), splitk_copies);
   w.splitk = splitk_copies > 0 ? c.take<char>(w.splitk_bytes) : nullptr;
   w.Om = resample ? c.take<TS>((size_t)l * m) : nullptr;
+  w.Ap1 = w.Bp1 = w.Ap2 = w.Bp2 = nullptr;
+  w.ea1 = w.eb1 = w.ea2 = w.eb2 = nullptr;
+  if (sizeof(TS) == sizeof(double) && f64tc > 0) {
+    const int kb = oz_k_pad(b);
+    w.Ap2 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(m, true), kb) / 2);
+    w.ea2 = c.take<int>(oz_rows_pad(m, true));
+    w.Bp2 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(n, false), kb) / 2);
+    w.eb2 = c.take<int>(oz_rows_pad(n, false));
+    if (f64tc > 1) {
+      const int km = oz_k_pad(m);
+      w.Ap1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(n, true), km) / 2);
+      w.ea1 = c.take<int>(oz_rows_pad(n, true));
+      w.Bp1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(b, false), km) / 2);
+      w.eb1 = c.take<int>(oz_rows_pad(b, false));
+    }
+  }
   w.bytes = align_up(c.off, 256);
   return w;
 }
@@ -219,10 +269,10 @@ cudaError_t prod_nn(const Ctx& c, int M, int N, int K, TS alpha, const TS* A, in
 template <typename TS>
 int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool pivot, int m, int n, TS* A, int lda,
                   int b, int p, int k, const TS* Omega, int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st,
-                  const uint64_t* rs_seed, int splitk_copies) {
+                  const uint64_t* rs_seed, int splitk_copies, int f64tc) {
   const int l = pivot ? b + p : 1;
   const bool rs = pivot && rs_seed != nullptr;
-  FactorWs<TS> w = carve_factor<TS>(ws, m, n, b, l, num_sms, rs, splitk_copies);
+  FactorWs<TS> w = carve_factor<TS>(ws, m, n, b, l, num_sms, rs, splitk_copies, f64tc);
   Ctx c{st, num_sms, launches, w.err, w.bar, w.splitk, w.splitk_bytes};
   cudaError_t e = cudaMemsetAsync(w.bar, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -279,8 +329,32 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
         Phase ph(h, st, RQ_PHASE_TRAILING, 4.0 * mt * (double)n2 * bj + 2.0 * mt * (double)bj * bj,
                  sz * (3.0 * mt * (double)n2 + 2.0 * bj * (double)n2 + 3.0 * mt * (double)bj));
         e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, ldy, Tm, b, TS(0), w.YT, ldy);
-        if (e == cudaSuccess) e = prod_tn_skinny<TS>(c, bj, n2, mt, w.YT, ldy, A2, lda, w.Wt, b);
-        if (e == cudaSuccess) e = prod_nn<TS>(c, mt, n2, bj, TS(-1), w.Ybuf, ldy, w.Wt, b, TS(1), A2, lda);
+        if (w.Ap1) {
+          // W = A2^T (Y T) on the tensor cores (FP64 through slices), stored as W^T (bj x n2, ld b)
+          const int Mp = oz_rows_pad(n2, true), Np = oz_rows_pad(bj, false), Kp = oz_k_pad(mt);
+          const double* A2d = reinterpret_cast<const double*>(A2);
+          if (e == cudaSuccess) e = oz_slice(c, true, n2, mt, A2d, lda, Mp, Kp, w.Ap1, w.ea1);
+          if (e == cudaSuccess)
+            e = oz_slice(c, true, bj, mt, reinterpret_cast<const double*>(w.YT), ldy, Np, Kp, w.Bp1, w.eb1);
+          if (e == cudaSuccess)
+            e = oz_gemm(c, n2, bj, mt, w.Ap1, Mp, w.ea1, w.Bp1, Np, w.eb1, Kp, 1.0, 0.0,
+                        reinterpret_cast<double*>(w.Wt), b, 1);
+        } else if (e == cudaSuccess) {
+          e = prod_tn_skinny<TS>(c, bj, n2, mt, w.YT, ldy, A2, lda, w.Wt, b);
+        }
+        if (w.Ap2) {
+          // A2 -= Y W^T on the tensor cores: operand rows are Y's rows and W^T's columns, K = bj
+          const int Mp = oz_rows_pad(mt, true), Np = oz_rows_pad(n2, false), Kp = oz_k_pad(bj);
+          if (e == cudaSuccess)
+            e = oz_slice(c, false, mt, bj, reinterpret_cast<const double*>(w.Ybuf), ldy, Mp, Kp, w.Ap2, w.ea2);
+          if (e == cudaSuccess)
+            e = oz_slice(c, true, n2, bj, reinterpret_cast<const double*>(w.Wt), b, Np, Kp, w.Bp2, w.eb2);
+          if (e == cudaSuccess)
+            e = oz_gemm(c, mt, n2, bj, w.Ap2, Mp, w.ea2, w.Bp2, Np, w.eb2, Kp, -1.0, 1.0,
+                        reinterpret_cast<double*>(A2), 1, lda);
+        } else if (e == cudaSuccess) {
+          e = prod_nn<TS>(c, mt, n2, bj, TS(-1), w.Ybuf, ldy, w.Wt, b, TS(1), A2, lda);
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "trailing update");
       }
       if (rs && j0 + bj < k) {
@@ -323,27 +397,34 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
 }
 
 template <typename TS>
-size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies) {
-  return carve_factor<TS>(nullptr, m, n, b, pivot ? b + p : 1, num_sms, pivot && resample, splitk_copies).bytes;
+size_t factor_ws_bytes(int m, int n, int b, int p, int num_sms, bool pivot, bool resample, int splitk_copies,
+                       int f64tc) {
+  return carve_factor<TS>(nullptr, m, n, b, pivot ? b + p : 1, num_sms, pivot && resample, splitk_copies, f64tc)
+      .bytes;
 }
 
 template int factor_blocks<float>(rq_handle, void*, int, long long*, bool, int, int, float*, int, int, int, int,
-                                  const float*, int, float*, int*, int*, cudaStream_t, const uint64_t*, int);
+                                  const float*, int, float*, int*, int*, cudaStream_t, const uint64_t*, int, int);
 template int factor_blocks<double>(rq_handle, void*, int, long long*, bool, int, int, double*, int, int, int, int,
-                                   const double*, int, double*, int*, int*, cudaStream_t, const uint64_t*, int);
-template size_t factor_ws_bytes<float>(int, int, int, int, int, bool, bool, int);
-template size_t factor_ws_bytes<double>(int, int, int, int, int, bool, bool, int);
+                                   const double*, int, double*, int*, int*, cudaStream_t, const uint64_t*, int, int);
+template size_t factor_ws_bytes<float>(int, int, int, int, int, bool, bool, int, int);
+template size_t factor_ws_bytes<double>(int, int, int, int, int, bool, bool, int, int);
 
 namespace {
+
+// The FP64 tensor-core mode of the handle's factorisations (0 when the driver
+// has no tensor-map encoder).
+int f64_tc_mode(rq_handle h) { return oz_supported() ? h->f64_tc : 0; }
 
 // The handle's factorisation: grows the handle's workspace, then the block loop.
 template <typename TS>
 int run_factor(rq_handle h, bool pivot, int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega,
                int ldo, TS* tau, int* jpvt, int* info, cudaStream_t st, const uint64_t* rs_seed = nullptr) {
-  int rc = ensure_ws(h, factor_ws_bytes<TS>(m, n, b, p, h->num_sms, pivot, rs_seed != nullptr, 16));
+  const int f64tc = f64_tc_mode(h);
+  int rc = ensure_ws(h, factor_ws_bytes<TS>(m, n, b, p, h->num_sms, pivot, rs_seed != nullptr, 16, f64tc));
   if (rc) return rc;
   return factor_blocks<TS>(h, h->ws, h->num_sms, &h->launches, pivot, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt,
-                           info, st, rs_seed, 16);
+                           info, st, rs_seed, 16, f64tc);
 }
 
 // Workspace of truncated RQRCP (Alg. 5).
@@ -772,6 +853,12 @@ int rq_create(rq_handle* out) {
   h->last_error[0] = 0;
   h->tile_m = kDefaultTile;
   h->tile_n = kDefaultTile;
+  {
+    // RQ_F64_TC: "0" keeps the FP64 block reflector products on the FP64 pipe,
+    // "1" moves the update A2 -= Y W^T to the tensor cores; default: both products
+    const char* v = getenv("RQ_F64_TC");
+    h->f64_tc = (v && v[0] == '0') ? 0 : (v && v[0] == '1') ? 1 : 2;
+  }
   h->prof_on = false;
   h->ev_used = 0;
   for (int i = 0; i < RQ_NUM_PHASES; ++i) h->prof_flops[i] = h->prof_bytes[i] = 0.0;
@@ -799,7 +886,7 @@ int rq_workspace_size(rq_handle h, int op, int prec, int m, int n, int k, int b,
   const int l = (op == RQ_OP_QR) ? 1 : b + p;
   if (op == RQ_OP_RQRCP || op == RQ_OP_QR || op == RQ_OP_RSRQRCP) {
     const bool rs = op == RQ_OP_RSRQRCP;
-    *bytes = prec == RQ_FP64 ? carve_factor<double>(nullptr, m, n, b, l, h->num_sms, rs).bytes
+    *bytes = prec == RQ_FP64 ? carve_factor<double>(nullptr, m, n, b, l, h->num_sms, rs, 16, f64_tc_mode(h)).bytes
                              : carve_factor<float>(nullptr, m, n, b, l, h->num_sms, rs).bytes;
     return RQ_OK;
   }
@@ -1134,6 +1221,49 @@ int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, cons
     if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, err, sizeof(int), cudaMemcpyDeviceToDevice, st);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rq_gemm_bf16");
+  return RQ_OK;
+}
+
+int rq_gemm_f64(rq_handle h, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                int ldc, int* info, rq_stream stream) {
+  if (!valid(h)) return RQ_EHANDLE;
+  if (M < 1) return -2;
+  if (N < 1) return -3;
+  if (K < 1) return -4;
+  if (!A) return -5;
+  if (lda < M) return -6;
+  if (!B) return -7;
+  if (ldb < K) return -8;
+  if (!C) return -9;
+  if (ldc < M) return -10;
+  {
+    const auto lo = [](const double* x) { return reinterpret_cast<uintptr_t>(x); };
+    const auto hi = [](const double* x, int ld, int rows, int cols) {
+      return reinterpret_cast<uintptr_t>(x) + sizeof(double) * ((size_t)ld * (cols - 1) + rows);
+    };
+    const uintptr_t c0 = lo(C), c1 = hi(C, ldc, M, N);
+    if ((c0 < hi(A, lda, M, K) && lo(A) < c1) || (c0 < hi(B, ldb, K, N) && lo(B) < c1)) return -9;
+  }
+  if (!oz_supported()) return fail(h, RQ_ENOTIMPL, "rq_gemm_f64: no tensor-map encoder in this driver");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Mp = oz_rows_pad(M, true), Np = oz_rows_pad(N, false), Kp = oz_k_pad(K);
+  Carver cv(nullptr);
+  OzWs z = carve_oz(cv, Mp, Np, Kp, (size_t)M * N);
+  const int rc = ensure_ws(h, align_up(cv.off, 256));
+  if (rc) return rc;
+  Carver cw(h->ws);
+  z = carve_oz(cw, Mp, Np, Kp, (size_t)M * N);
+  Ctx c{st, h->num_sms, &h->launches, z.err, z.bar, z.split, z.split_bytes};
+  cudaError_t e;
+  {
+    Phase ph(h, st, RQ_PHASE_OTHER, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    e = cudaMemsetAsync(z.bar, 0, 16, st);
+    if (e == cudaSuccess) e = oz_slice(c, false, M, K, A, lda, Mp, Kp, z.Ap, z.ea);
+    if (e == cudaSuccess) e = oz_slice(c, true, N, K, B, ldb, Np, Kp, z.Bp, z.eb);
+    if (e == cudaSuccess) e = oz_gemm(c, M, N, K, z.Ap, Mp, z.ea, z.Bp, Np, z.eb, Kp, 1.0, 0.0, C, 1, ldc);
+    if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, z.err, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "rq_gemm_f64");
   return RQ_OK;
 }
 

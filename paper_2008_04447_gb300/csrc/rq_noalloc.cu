@@ -9,7 +9,9 @@
 //
 // The factorisation is the one rq_rqrcp runs (the same block loop,
 // factor_blocks), over the fixed array instead of a handle's workspace, with
-// fewer split-K partial copies (none in FP64) to keep the array modest.
+// fewer split-K partial copies (none in FP64) and, in FP64, the block
+// reflector products on the FP64 pipe (the tensor-core path's slice planes
+// would not fit), to keep the array modest.
 //
 // The scratch array is RQ_NOALLOC_SCRATCH_BYTES large and every GPU that
 // loads this library holds it until the process exits.  All calls share it:
@@ -56,11 +58,11 @@ int run(int m, int n, TS* A, int lda, int b, int p, int k, const TS* Omega, int 
   int sms = 0;
   int rc = setup(&base, &sms);
   if (rc) return rc;
-  if (factor_ws_bytes<TS>(m, n, b, p, sms, true, false, kSplitCopies<TS>) > (size_t)RQ_NOALLOC_SCRATCH_BYTES)
+  if (factor_ws_bytes<TS>(m, n, b, p, sms, true, false, kSplitCopies<TS>, 0) > (size_t)RQ_NOALLOC_SCRATCH_BYTES)
     return RQ_ETOOBIG;
   // factor_blocks clears the barrier words first: the array keeps the previous call's contents
   return factor_blocks<TS>(nullptr, base, sms, &g_launches, true, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info,
-                           st, nullptr, kSplitCopies<TS>);
+                           st, nullptr, kSplitCopies<TS>, 0);
 }
 
 }  // namespace

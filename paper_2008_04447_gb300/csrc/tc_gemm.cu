@@ -34,66 +34,15 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace rq {
 namespace {
+using namespace tc;
 
 constexpr int TBM = 128;  // tile rows (M) = TMEM lanes
 constexpr int TBK = 32;   // K slice: 32 FP32 = one 128-byte swizzle row
 constexpr int kTcThreads = 192;
-constexpr long long kWaitLimit = 1ll << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// Bounded wait for the phase of parity `par` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par, int* err) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(par)
-        : "memory");
-    if (ok) return true;
-    if ((i & 1023) == 1023 && *reinterpret_cast<volatile int*>(err) != 0) return false;
-  }
-  atomicCAS(err, 0, RQ_ETIMEOUT);
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
-}
 
 // Instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = bn.
 __host__ __device__ constexpr uint32_t tf32_idesc(int bn) {
@@ -106,10 +55,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, u
           dtm),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -366,26 +311,6 @@ __global__ void __launch_bounds__(kTcThreads)
   }
 }
 
-using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, looked up once per process (a function-local
-// static: its initialisation is thread safe); nullptr if the driver lacks it.
-EncodeFn encoder() {
-  static const EncodeFn fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      return reinterpret_cast<EncodeFn>(p);
-    cudaGetLastError();
-    return static_cast<EncodeFn>(nullptr);
-  }();
-  return fn;
-}
-
 // 2-D K-major map over a column-major (rows = K) matrix: box {32, box_rows}.
 bool make_map(CUtensorMap* map, const float* base, int K, int cols, int ld, int box_rows) {
   EncodeFn enc = encoder();
@@ -441,7 +366,7 @@ cudaError_t tc_dispatch(const Ctx& c, int bn, int K, const CUtensorMap& ma, cons
 }  // namespace
 
 bool tc_gemm_supported(const float* A, int lda, const float* B, int ldb) {
-  return encoder() != nullptr && (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+  return tc::encoder() != nullptr && (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
          (reinterpret_cast<uintptr_t>(B) % 16 == 0) && lda % 4 == 0 && ldb % 4 == 0;
 }
 

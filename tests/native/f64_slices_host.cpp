@@ -18,7 +18,7 @@ void f64s_slices(const double* x, const int* e, int n, int* s) {
 
 int f64s_acc_unit(int K) { return rq::f64_acc_unit(K); }
 
-// P: nchunks x levels (L = 2 .. 8 in order) exact partials; returns the accumulator.
+// P: nchunks x levels (L = 2 .. 9 in order) exact partials; returns the accumulator.
 long long f64s_combine(const float* P, int nchunks, int u) {
   int64_t acc = 0;
   for (int c = 0; c < nchunks; ++c)
