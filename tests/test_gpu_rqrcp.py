@@ -139,3 +139,38 @@ def test_bad_arguments_return_negative_index(H):
     assert _lib.rq_rqrcp(H.h, 7, 4, 4, A, 4, 2, 2, 4, A, 4, t, j, i) == -2   # precision
     assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, _lib.RQ_MAX_B + 1, 2, 4, A, 4, t, j, i) == -7   # b > RQ_MAX_B
     assert _lib.rq_rqrcp(H.h, 0, 4, 4, A, 4, 2, _lib.RQ_MAX_L - 1, 4, A, 4, t, j, i) == -8   # b + p > RQ_MAX_L
+
+
+@pytest.mark.parametrize("mode", ["0", "1"])
+def test_fp64_update_engines_agree(mode):
+    """The FP64 block reflector products on the bfloat16 tensor cores (the
+    default) and on the FP64 pipe (RQ_F64_TC=0) or with only the update on the
+    tensor cores (RQ_F64_TC=1) give the same factorisation: identical pivots
+    and R within 1e-12 ||A||_F, and each matches the oracle."""
+    import os
+    import torch
+    from paper_2008_04447_gb300 import Handle, build
+    build.build()
+    m, n, b, p = 700, 600, 32, 8
+    a = I.graded(m, n, 8, seed=31)
+    om = I.omega(b + p, m, seed=32)
+    outs = {}
+    for md in ("2", mode):
+        old = os.environ.get("RQ_F64_TC")
+        os.environ["RQ_F64_TC"] = md
+        try:
+            h = Handle()
+        finally:
+            if old is None:
+                del os.environ["RQ_F64_TC"]
+            else:
+                os.environ["RQ_F64_TC"] = old
+        outs[md] = run_gpu_rqrcp(h, a, om, b, p)
+        h.close()
+    ref = O.rqrcp(a, om, b)
+    nrm = np.linalg.norm(a)
+    for md, (F, tau, jpvt, info) in outs.items():
+        assert np.array_equal(jpvt, ref.jpvt), md
+        assert np.max(np.abs(np.triu(F) - np.triu(ref.F))) <= 1e-12 * nrm, md
+    assert np.array_equal(outs["2"][2], outs[mode][2])
+    assert np.max(np.abs(np.triu(outs["2"][0]) - np.triu(outs[mode][0]))) <= 1e-12 * nrm
