@@ -141,11 +141,31 @@ def run_sweep(args):
             torch.cuda.empty_cache()
 
 
-# DRAM bytes moved per factorisation by the trailing-update kernels (the W^T
-# GEMM, the A2 update GEMM and the split-K reduce) of the FP64 16384 x 16384
-# workload, from the ncu capture summarised in
-# profiles/rqrcp_fp64_16384_launches.md (valid while those kernels are unchanged).
-TRAILING_DRAM_BYTES_FP64_16384 = 556.3e9
+def bf16_peak_tflops():
+    """(TFLOP/s, source): the measured sustained bfloat16 dense rate of
+    MEASURED_PEAKS.json (the trailing update runs inside a seconds-long step),
+    else the sustained figure the profiling notes give as the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        for key in ("bf16_tflops_sustained", "bf16_tflops"):
+            if key in d:
+                return float(d[key]), f"MEASURED_PEAKS.json {key} (measured cuBLAS bf16)"
+    except (OSError, KeyError, ValueError):
+        pass
+    return 1700.0, "fallback: 1.7 PFLOP/s, an earlier sustained GB300 bf16 measurement"
+
+
+def slice_pair_flops(m, n, b, k=None):
+    """bfloat16 tensor-core flops of the FP64 trailing update through slices:
+    36 slice-pair products for each of the two block reflector products
+    (W^T = (Y T)^T A2 and A2 -= Y W^T, 2 m_t n2 b_J flops each) per block."""
+    k = min(m, n) if k is None else k
+    tot = 0.0
+    for j0 in range(0, k, b):
+        bj = min(b, k - j0)
+        tot += 2 * 2.0 * (m - j0) * (n - j0 - bj) * bj
+    return 36.0 * tot
 
 
 def flops_qr(m, n):
@@ -837,14 +857,24 @@ def main():
                   "gbs": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None, "launches": v[3] // args.steps}
               for k, v in prof.items()}
     achieved = tr[1] / (tr[0] / 1e3) / 1e12 if tr[0] > 0 else None
-    measured = args.prec == "fp64" and n == 16384 and b == 64
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": TRAILING_DRAM_BYTES_FP64_16384 if measured else None,
-                "traffic_scope": "DRAM bytes per step of all trailing-update launches (ncu)",
-                "algorithmic_bytes": tr[2] / args.steps,
-                "kernel": "trailing update (block reflector GEMMs), FP64",
-                "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop (FP64 pipe, nominal)"}
+    f64_tc = args.prec == "fp64" and os.environ.get("RQ_F64_TC", "2")[:1] not in ("0", "1")
+    if f64_tc and tr[0] > 0:
+        # the FP64 block reflector products run as bfloat16 slice-pair MMAs (oz_gemm_kernel)
+        pk, pk_src = bf16_peak_tflops()
+        tc_rate = slice_pair_flops(m, n, b) * args.steps / (tr[0] / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": tc_rate, "peak": pk, "unit": "TFLOP/s", "frac": tc_rate / pk,
+                    "traffic": None,
+                    "kernel": "trailing update: oz_gemm_kernel (FP64 block reflector products as 36 bfloat16 "
+                              "slice-pair MMAs) + the Y T product; operand slicing is its own phase",
+                    "achieved_is": "bfloat16 slice-pair flops per second over the trailing phase's CUDA-event time",
+                    "fp64_equivalent_tflops": achieved, "frac_of_fp64_pipe": achieved / FP64_PEAK_TFLOPS,
+                    "algorithmic_bytes": tr[2] / args.steps, "peak_source": pk_src}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                    "algorithmic_bytes": tr[2] / args.steps,
+                    "kernel": "trailing update (block reflector GEMMs), FP64 pipe",
+                    "peak_source": "derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop (FP64 pipe, nominal)"}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -1005,7 +1035,8 @@ def main():
             pk = leg_fp64_peak()
             line["fp64_peak"] = pk
             if args.prec == "fp64" and achieved:
-                roofline["frac_of_cublas_dgemm"] = achieved / pk["cublas_dgemm_tflops"]
+                # FP64 rate of the trailing update over cuBLAS DGEMM's on this GPU
+                roofline["fp64_over_cublas_dgemm"] = achieved / pk["cublas_dgemm_tflops"]
         except Exception as exc:  # context only
             line["fp64_peak"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     if "slices" in legs:

@@ -106,7 +106,8 @@ long long rq_launch_count(rq_handle h);
 #define RQ_PHASE_TRAILING 4      /* W^T = T^T Y^T A2, A2 -= Y W^T (block reflector) */
 #define RQ_PHASE_SAMPLE_UPDATE 5 /* Eq. (update1) */
 #define RQ_PHASE_OTHER 6         /* TRQRCP / TUXV products, small kernels */
-#define RQ_NUM_PHASES 7
+#define RQ_PHASE_SLICE 7         /* FP64 operands cut into bfloat16 slices for the tensor cores */
+#define RQ_NUM_PHASES 8
 
 /* Enable (1) or disable (0) per-phase timing: CUDA events are recorded on the
  * call's stream around each phase.  Adds two event records per phase. */
@@ -148,7 +149,13 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  *   info   device int32 (out): 0, or j > 0 when R(j-1, j-1) is exactly zero
  *          (first such j; the factorisation still completes).
  * Precisions: RQ_FP64 and RQ_FP32 (RQ_MIXED returns RQ_ENOTIMPL: the BF16
- * sketch serves the truncated paths).
+ * sketch serves the truncated paths).  In FP64 the two block reflector
+ * products of every block (W^T = (Y T)^T A2 and A2 -= Y W^T) run on the
+ * bfloat16 tensor cores through the exact slice split of rq_gemm_f64, which
+ * keeps FP64 accuracy; the handle's workspace then also holds the slices of
+ * A2, about 16 m n bytes (the environment variable RQ_F64_TC, read when the
+ * handle is created, selects "0": both products on the FP64 pipe, "1": only
+ * the update on the tensor cores).  rq_qr and rq_rsrqrcp do the same.
  */
 int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
              const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);

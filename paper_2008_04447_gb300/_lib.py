@@ -28,7 +28,7 @@ RQ_MAX_B, RQ_MAX_L = 256, 384
 
 RQ_FP64, RQ_FP32, RQ_MIXED = 0, 1, 2
 RQ_OP_RQRCP, RQ_OP_TRQRCP, RQ_OP_TUXV, RQ_OP_QR, RQ_OP_RSRQRCP = 0, 1, 2, 3, 4
-PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing", "sample_update", "other"]
+PHASES = ["sketch", "sample_qrcp", "permute", "panel", "trailing", "sample_update", "other", "slice"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

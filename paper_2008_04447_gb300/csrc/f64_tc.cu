@@ -17,13 +17,17 @@
 //   levels are drained into int64 registers in units of 2^u, and at the end
 //   the int64 sums return to FP64 with one rounding and the two exponents.
 //
-// Kernel: one CTA per 128 x 64 tile of D (and K range, for split-K).
-//   warp 0     : TMA producer (eight A planes of 128 x 64 and eight B planes of
-//                64 x 64 per 64-step K stage: 192 KB, one stage)
-//   warp 1     : TMEM allocation and the single-thread tcgen05.mma issue
-//   warps 2..9 : drain TMEM into int64 accumulators (warp w reads TMEM lane
-//                quarter w % 4, columns 32 ((w - 2) / 4) ..), then the FP64
-//                epilogue C = alpha D + beta C
+// Kernel: persistent, one CTA per SM; a CTA takes 128 x 64 tiles of D (and
+// K ranges, for split-K) one after another.
+//   warp 0     : TMA producer: per 32-step K stage the eight A planes (128 x 32)
+//                and eight B planes (64 x 32), 96 KB, into a two-stage ring
+//   warp 1     : TMEM allocation and the single-thread tcgen05.mma issue, level
+//                by level; the first MMA of a chunk into level L waits until
+//                the drain warps have read level L of the previous chunk
+//   warps 2..9 : drain TMEM level by level into int64 accumulators (warp w
+//                reads TMEM lane quarter w % 4, columns 32 ((w - 2) / 4) ..),
+//                and after a tile's last chunk the FP64 epilogue
+//                C = alpha D + beta C, while the MMAs of the next tile run
 // All waits are bounded: on a timeout the kernel records RQ_ETIMEOUT, lets its
 // copies land, frees its TMEM and returns.
 #include <cuda.h>
@@ -41,16 +45,30 @@ using namespace tc;
 
 constexpr int OZ_BM = 128;                       // tile rows = TMEM lanes
 constexpr int OZ_BN = 64;                        // tile columns
-constexpr int OZ_BK = 64;                        // K per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int OZ_BK = 32;                        // K per stage: 32 bf16 = one 64-byte swizzle row
+constexpr int OZ_NS = 2;                         // stages in the ring
 constexpr int OZ_S = kF64Slices;                 // 8 slices
 constexpr int OZ_THREADS = 320;
-constexpr uint32_t OZ_ABYTES = OZ_BM * OZ_BK * 2;             // one A plane tile: 16 KB
-constexpr uint32_t OZ_BBYTES = OZ_BN * OZ_BK * 2;             // one B plane tile: 8 KB
-constexpr uint32_t OZ_STAGE = OZ_S * (OZ_ABYTES + OZ_BBYTES); // 192 KB
+constexpr uint32_t OZ_ABYTES = OZ_BM * OZ_BK * 2;             // one A plane tile: 8 KB
+constexpr uint32_t OZ_BBYTES = OZ_BN * OZ_BK * 2;             // one B plane tile: 4 KB
+constexpr uint32_t OZ_STAGE = OZ_S * (OZ_ABYTES + OZ_BBYTES); // 96 KB
 constexpr uint32_t OZ_TMEM_COLS = OZ_S * OZ_BN;               // 512
-constexpr int OZ_STAGES_PER_CHUNK = kF64ChunkK / OZ_BK;       // 2 stages between drains
+constexpr int OZ_STAGES_PER_CHUNK = kF64ChunkK / OZ_BK;       // 4 stages between drains
+constexpr int OZ_KPAD = 64;                                   // planes' K padding
 
 static_assert(OZ_TMEM_COLS == 512, "one 64-column accumulator per level fills TMEM");
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512
+// bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // 64-byte swizzle
+  return d;
+}
 
 // Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = 64.
 __host__ __device__ constexpr uint32_t bf16_idesc() {
@@ -65,13 +83,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, u
       : "memory");
 }
 
-// 2^e as an FP64 value (e in the normal range).
-__device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// acc += P 2^sh (sh >= 0) or P 2^sh rounded to nearest (sh < 0): f64_add_level's
+// arithmetic with P, an exact integer below 2^24 held in FP32, converted
+// through int32 (a 32-bit conversion; the 64-bit one runs on the FP64 pipe).
+__device__ __forceinline__ void add_level_fast(int64_t& acc, float P, int sh) {
+  const int64_t p = static_cast<int64_t>(__float2int_rz(P));
+  if (sh >= 0)
+    acc += p << sh;
+  else if (sh > -40)
+    acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
+}
+
+// v 2^ex, exactly: the exponent field moves when v and the result are normal
+// (integer arithmetic, no FP64 multiply), else ldexp.
+__device__ __forceinline__ double scale_pow2(double v, int ex) {
+  const long long b = __double_as_longlong(v);
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  if (E > 0 && E + ex > 0 && E + ex < 2047) return __longlong_as_double(b + (static_cast<long long>(ex) << 52));
+  return v == 0.0 ? v : ldexp(v, ex);
+}
 
 struct OzArgs {
   int M, N, K;              // D = A B^T: A M x K, B N x K
   int Mp, Np;               // plane row counts (the row offset of plane s is s Mp, s Np)
-  int kchunk;               // K range of blockIdx.z (a multiple of OZ_BK)
+  int kchunk;               // K range of one split-K part (a multiple of kF64ChunkK)
+  int S;                    // split-K parts
   int u;                    // accumulator unit exponent, >= f64_acc_unit(K)
   const int* ea;            // M row exponents of A
   const int* eb;            // N row exponents of B
@@ -86,24 +122,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t bars[4];
+  // full[2], empty[2], dfull, ldrained[8]
+  __shared__ __align__(8) uint64_t bars[2 * OZ_NS + 1 + OZ_S];
   __shared__ uint32_t s_tmem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
-  const int kbeg = blockIdx.z * a.kchunk;
-  const int kend = min(a.K, kbeg + a.kchunk);
-  const int nk = (kend - kbeg + OZ_BK - 1) / OZ_BK;
-  const int nchunks = (nk + OZ_STAGES_PER_CHUNK - 1) / OZ_STAGES_PER_CHUNK;
+  const int tiles_m = a.Mp / OZ_BM, tiles_n = a.Np / OZ_BN;
+  const int items = tiles_m * tiles_n * a.S;
   const uint32_t bar0 = smem_u32(bars);
-  const uint32_t full = bar0, empty = bar0 + 8, dfull = bar0 + 16, dempty = bar0 + 24;
-  unsigned char* sA = sm;                          // plane s at sA + s OZ_ABYTES
-  unsigned char* sB = sm + OZ_S * OZ_ABYTES;       // plane s at sB + s OZ_BBYTES
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (OZ_NS + s); };
+  const uint32_t dfull = bar0 + 8u * (2 * OZ_NS);
+  auto ldrained = [&](int L) { return bar0 + 8u * (2 * OZ_NS + 1 + L); };
+  auto sA = [&](int s, int i) { return sm + (size_t)s * OZ_STAGE + (size_t)i * OZ_ABYTES; };
+  auto sB = [&](int s, int j) { return sm + (size_t)s * OZ_STAGE + OZ_S * OZ_ABYTES + (size_t)j * OZ_BBYTES; };
+  // item w -> tile (tm, tn) and K range z (tm fastest)
+  auto item = [&](int w, int& m0, int& n0, int& kbeg, int& nk) {
+    const int tm = w % tiles_m;
+    const int rest = w / tiles_m;
+    const int tn = rest % tiles_n, z = rest / tiles_n;
+    m0 = tm * OZ_BM;
+    n0 = tn * OZ_BN;
+    kbeg = z * a.kchunk;
+    const int kend = min(a.K, kbeg + a.kchunk);
+    nk = (kend - kbeg + OZ_BK - 1) / OZ_BK;
+  };
 
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(empty, 1);
+    for (int s = 0; s < OZ_NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
     mbar_init(dfull, 1);
-    mbar_init(dempty, 256);
+    for (int L = 0; L < OZ_S; ++L) mbar_init(ldrained(L), 256);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -119,93 +169,132 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int it = 0; it < nk; ++it) {
-        if (!mbar_wait(empty, (it & 1) ^ 1, a.err)) break;
-        mbar_expect_tx(full, OZ_STAGE);
-        const int k = kbeg + it * OZ_BK;
+      long long g = 0;  // stages issued so far (all items)
+      bool ok = true;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+        int m0, n0, kbeg, nk;
+        item(w, m0, n0, kbeg, nk);
+        for (int it = 0; it < nk; ++it, ++g) {
+          const int s = (int)(g % OZ_NS);
+          if (!mbar_wait(empty(s), (uint32_t)((g / OZ_NS) & 1) ^ 1u, a.err)) { ok = false; break; }
+          mbar_expect_tx(full(s), OZ_STAGE);
+          const int k = kbeg + it * OZ_BK;
 #pragma unroll 1
-        for (int s = 0; s < OZ_S; ++s) {
-          tma_load_2d(smem_u32(sA + s * OZ_ABYTES), &mapA, k, s * a.Mp + m0, full);
-          tma_load_2d(smem_u32(sB + s * OZ_BBYTES), &mapB, k, s * a.Np + n0, full);
+          for (int i = 0; i < OZ_S; ++i) {
+            tma_load_2d(smem_u32(sA(s, i)), &mapA, k, i * a.Mp + m0, full(s));
+            tma_load_2d(smem_u32(sB(s, i)), &mapB, k, i * a.Np + n0, full(s));
+          }
         }
-        issued = it + 1;
       }
-      // let the last copy land before the CTA may exit
-      if (issued > 0) mbar_wait(full, (issued - 1) & 1, a.err);
+      // let the copies still in flight land before the CTA may exit
+      for (long long q = (g > OZ_NS ? g - OZ_NS : 0); q < g; ++q)
+        mbar_wait(full((int)(q % OZ_NS)), (uint32_t)((q / OZ_NS) & 1), a.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = bf16_idesc();
-      for (int it = 0; it < nk; ++it) {
-        const int st = it % OZ_STAGES_PER_CHUNK;
-        const int c = it / OZ_STAGES_PER_CHUNK;
-        // the first stage of a chunk overwrites the levels: the previous chunk must be drained
-        if (st == 0 && c > 0 && !mbar_wait(dempty, (c - 1) & 1, a.err)) break;
-        if (!mbar_wait(full, it & 1, a.err)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      long long g = 0;   // stages consumed (all items)
+      long long gc = 0;  // chunks issued (all items)
+      bool ok = true;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+        int m0, n0, kbeg, nk;
+        item(w, m0, n0, kbeg, nk);
+        for (int it = 0; it < nk && ok; ++it, ++g) {
+          const int s = (int)(g % OZ_NS);
+          const int st = it % OZ_STAGES_PER_CHUNK;
+          if (!mbar_wait(full(s), (uint32_t)((g / OZ_NS) & 1), a.err)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-        for (int i = 0; i < OZ_S; ++i) {
-          const uint32_t ai = smem_u32(sA + i * OZ_ABYTES);
+          for (int L = 0; L < OZ_S && ok; ++L) {
+            // the first stage of a chunk overwrites level L: the previous chunk's level L must be drained
+            if (st == 0 && gc > 0) {
+              if (!mbar_wait(ldrained(L), (uint32_t)((gc - 1) & 1), a.err)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint32_t d = tmem + (uint32_t)(L * OZ_BN);
 #pragma unroll 1
-          for (int j = 0; j + i < OZ_S; ++j) {
-            const uint32_t bj = smem_u32(sB + j * OZ_BBYTES);
-            const uint32_t d = tmem + (uint32_t)((i + j) * OZ_BN);
+            for (int i = 0; i <= L; ++i) {
+              const uint32_t ai = smem_u32(sA(s, i));
+              const uint32_t bj = smem_u32(sB(s, L - i));
 #pragma unroll
-            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-              // the pair (0, L) opens level L in each chunk
-              const uint32_t acc = (st == 0 && i == 0 && kk == 0) ? 0u : 1u;
-              mma_bf16(d, sw128_desc(ai + kk * 32), sw128_desc(bj + kk * 32), idesc, acc);
+              for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                // the pair (0, L) opens level L in each chunk
+                const uint32_t acc = (st == 0 && i == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(d, sw64_desc(ai + kk * 32), sw64_desc(bj + kk * 32), idesc, acc);
+              }
             }
           }
+          if (!ok) break;
+          mma_commit(empty(s));
+          if (st == OZ_STAGES_PER_CHUNK - 1 || it == nk - 1) {
+            mma_commit(dfull);
+            ++gc;
+          }
         }
-        mma_commit(empty);
-        if (st == OZ_STAGES_PER_CHUNK - 1 || it == nk - 1) mma_commit(dfull);
       }
     }
   } else {
-    // warps 2..9: drain every chunk into int64, then the FP64 epilogue
+    // warps 2..9: drain every chunk into int64, then the FP64 epilogue of the tile
     const int q = warp & 3;           // TMEM lane quarter this warp may read
     const int h = (warp - 2) >> 2;    // column half
-    const int row = m0 + q * 32 + lane;
-    int64_t acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    long long gc = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(dfull, c & 1, a.err)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-      for (int L = 0; L < OZ_S; ++L) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(L * OZ_BN + 32 * h);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+      int m0, n0, kbeg, nk;
+      item(w, m0, n0, kbeg, nk);
+      const int nchunks = (nk + OZ_STAGES_PER_CHUNK - 1) / OZ_STAGES_PER_CHUNK;
+      const int row = m0 + q * 32 + lane;
+      int64_t acc[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) f64_add_level(acc[j], __uint_as_float(r[j]), L + 2, a.u);
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        if (!mbar_wait(dfull, (uint32_t)(gc & 1), a.err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int L = 0; L < OZ_S; ++L) {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(L * OZ_BN + 32 * h);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // level L is in registers: the next chunk's MMAs may overwrite it
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(ldrained(L));
+          // level L = 2 + L of f64_add_level, unit 2^u
+          const int sh = 112 - kF64SliceBits * (L + 2) - a.u;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) add_level_fast(acc[j], __uint_as_float(r[j]), sh);
+        }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(dempty);
-    }
-    if (ok && row < a.M) {
-      const int er = a.ea[row] + a.u - 112;
-      double* C = a.C + blockIdx.z * a.czs;
+      if (!ok) break;
+      if (row < a.M) {
+        const int er = a.ea[row] + a.u - 112;
+        double* C = a.C + (size_t)(w / (tiles_m * tiles_n)) * a.czs + (long long)row * a.rs;
+        const int col0 = n0 + 32 * h;
+        // C = alpha D + beta C with the common cases (beta 0 or 1, alpha +-1) free of FP64 multiplies
+        const int mode = a.beta == 0.0 ? (a.alpha == 1.0 ? 0 : 1) : (a.beta == 1.0 && a.alpha == -1.0 ? 2 : 3);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = n0 + 32 * h + j;
-        if (col < a.N) {
-          const int ex = er + a.eb[col];
-          double v = static_cast<double>(acc[j]);
-          v = (ex >= -1022 && ex <= 1023) ? v * pow2i(ex) : ldexp(v, ex);
-          double* out = C + (long long)row * a.rs + (long long)col * a.cs;
-          *out = a.beta != 0.0 ? fma(a.alpha, v, a.beta * *out) : a.alpha * v;
+        for (int j = 0; j < 32; ++j) {
+          const int col = col0 + j;
+          if (col < a.N) {
+            const double v = scale_pow2(static_cast<double>(acc[j]), er + a.eb[col]);
+            double* out = C + (long long)col * a.cs;
+            if (mode == 0)
+              *out = v;
+            else if (mode == 1)
+              *out = a.alpha * v;
+            else if (mode == 2)
+              *out = *out - v;
+            else
+              *out = fma(a.alpha, v, a.beta * *out);
+          }
         }
       }
     }
@@ -246,6 +335,43 @@ __global__ void slice_cols_kernel(int R, int K, const double* __restrict__ src, 
   const size_t pstride = (size_t)Rp * Kp;
   uint16_t* out = planes + (size_t)r * Kp;
   for (int k = lane; k < Kp; k += 32) {
+    const double x = (r < R && k < K) ? col[k] : 0.0;
+    int s[OZ_S];
+    f64_slices(x, ex, s);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(bf16_bits_of(s[i]));
+  }
+}
+
+// The same for long rows (K >= 1024): one 256-thread CTA per row.
+__global__ void __launch_bounds__(256) slice_cols_long_kernel(int R, int K, const double* __restrict__ src,
+                                                              long long ld, int Rp, int Kp,
+                                                              uint16_t* __restrict__ planes, int* __restrict__ e) {
+  __shared__ unsigned long long s_mx[8];
+  const int r = blockIdx.x;
+  const int t = threadIdx.x;
+  const double* col = src + (long long)r * ld;
+  unsigned long long mx = 0;
+  if (r < R)
+    for (int k = t; k < K; k += 256) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(col[k])) & 0x7fffffffffffffffull;
+      mx = b > mx ? b : mx;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((t & 31) == 0) s_mx[t >> 5] = mx;
+  __syncthreads();
+  mx = s_mx[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) mx = s_mx[w] > mx ? s_mx[w] : mx;
+  const int ex = f64_scale_exponent(__longlong_as_double(static_cast<long long>(mx)));
+  if (t == 0) e[r] = ex;
+  const size_t pstride = (size_t)Rp * Kp;
+  uint16_t* out = planes + (size_t)r * Kp;
+  for (int k = t; k < Kp; k += 256) {
     const double x = (r < R && k < K) ? col[k] : 0.0;
     int s[OZ_S];
     f64_slices(x, ex, s);
@@ -302,7 +428,7 @@ __global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__
   }
 }
 
-// 2-D map over the planes [8][rows_per_plane][Kp] bf16: box {64, box_rows}, 128-byte swizzle.
+// 2-D map over the planes [8][rows_per_plane][Kp] bf16: box {32, box_rows}, 64-byte swizzle.
 bool make_plane_map(CUtensorMap* map, const uint16_t* base, int Kp, int rows_total, int box_rows) {
   EncodeFn enc = encoder();
   if (!enc) return false;
@@ -311,23 +437,25 @@ bool make_plane_map(CUtensorMap* map, const uint16_t* base, int Kp, int rows_tot
   cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t oz_smem() { return OZ_STAGE + 1024; }
+size_t oz_smem() { return OZ_NS * OZ_STAGE + 1024; }
 
 }  // namespace
 
 int oz_rows_pad(int rows, bool a_side) { return a_side ? (rows + OZ_BM - 1) / OZ_BM * OZ_BM : (rows + OZ_BN - 1) / OZ_BN * OZ_BN; }
-int oz_k_pad(int K) { return (K + OZ_BK - 1) / OZ_BK * OZ_BK; }
+int oz_k_pad(int K) { return (K + OZ_KPAD - 1) / OZ_KPAD * OZ_KPAD; }
 size_t oz_plane_bytes(int rows_pad, int k_pad) { return (size_t)OZ_S * rows_pad * k_pad * sizeof(uint16_t); }
 bool oz_supported() { return encoder() != nullptr; }
 
 cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const double* src, long long ld, int Rp, int Kp,
                      uint16_t* planes, int* e) {
   if (Rp <= 0) return cudaSuccess;
-  if (k_along_columns) {
+  if (k_along_columns && K >= 1024) {
+    slice_cols_long_kernel<<<Rp, 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
+  } else if (k_along_columns) {
     slice_cols_kernel<<<(Rp + 7) / 8, 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
   } else {
     slice_rows_kernel<<<(Rp + 127) / 128, 128, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
@@ -359,6 +487,7 @@ cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int M
     S = (K + kchunk - 1) / kchunk;
   }
   OzArgs args;
+  args.S = S;
   args.M = M;
   args.N = N;
   args.K = K;
@@ -387,7 +516,8 @@ cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int M
   const size_t smem = oz_smem();
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(Mp / OZ_BM, Np / OZ_BN, S);
+  const int items = tiles * S;
+  const int grid = items < c.num_sms ? items : c.num_sms;
   oz_gemm_kernel<<<grid, OZ_THREADS, smem, c.stream>>>(ma, mb, args);
   ++*c.launches;
   e = cudaGetLastError();

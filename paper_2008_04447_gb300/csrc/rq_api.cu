@@ -90,7 +90,7 @@ int next_event(rq_handle h) {
 // profiling tool is attached), so timeline tools show the path's phases.
 const char* const kPhaseNames[RQ_NUM_PHASES] = {"rq sketch",         "rq sample QRCP",    "rq permute",
                                                 "rq panel",          "rq trailing update", "rq sample update",
-                                                "rq other"};
+                                                "rq other",          "rq FP64 slices"};
 
 struct Phase {
   rq_handle h;
@@ -157,6 +157,8 @@ struct FactorWs {
   // rows, W^T's columns)
   uint16_t *Ap1, *Bp1, *Ap2, *Bp2;
   int *ea1, *eb1, *ea2, *eb2;
+  uint16_t* Osl;  // slices of Omega for the FP64 sketch on the tensor cores (B = Omega A)
+  int* eo;
   size_t bytes;
 };
 
@@ -193,8 +195,8 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
   w.splitk_bytes = splitk_bytes_for(b, n, sizeof(TS), splitk_copies);
   w.splitk = splitk_copies > 0 ? c.take<char>(w.splitk_bytes) : nullptr;
   w.Om = resample ? c.take<TS>((size_t)l * m) : nullptr;
-  w.Ap1 = w.Bp1 = w.Ap2 = w.Bp2 = nullptr;
-  w.ea1 = w.eb1 = w.ea2 = w.eb2 = nullptr;
+  w.Ap1 = w.Bp1 = w.Ap2 = w.Bp2 = w.Osl = nullptr;
+  w.ea1 = w.eb1 = w.ea2 = w.eb2 = w.eo = nullptr;
   if (sizeof(TS) == sizeof(double) && f64tc > 0) {
     const int kb = oz_k_pad(b);
     w.Ap2 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(m, true), kb) / 2);
@@ -207,6 +209,10 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
       w.ea1 = c.take<int>(oz_rows_pad(n, true));
       w.Bp1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(b, false), km) / 2);
       w.eb1 = c.take<int>(oz_rows_pad(b, false));
+      if (l > 1 && !resample) {
+        w.Osl = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(l, true), km) / 2);
+        w.eo = c.take<int>(oz_rows_pad(l, true));
+      }
     }
   }
   w.bytes = align_up(c.off, 256);
@@ -290,7 +296,17 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
   if (pivot) {
     // Alg. 4: B = Omega A
     Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * l * (double)m * n, sz * ((double)m * n + (double)l * m + (double)l * n));
-    e = prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l);
+    if (w.Osl) {
+      // FP64 B = Omega A on the tensor cores: operand rows are Omega's rows and A's columns, K = m
+      const int Mp = oz_rows_pad(l, true), Np = oz_rows_pad(n, false), Kp = oz_k_pad(m);
+      e = oz_slice(c, false, l, m, reinterpret_cast<const double*>(Omega), ldo, Mp, Kp, w.Osl, w.eo);
+      if (e == cudaSuccess)
+        e = oz_slice(c, true, n, m, reinterpret_cast<const double*>(A), lda, Np, Kp, w.Ap1, w.ea1);
+      if (e == cudaSuccess)
+        e = oz_gemm(c, l, n, m, w.Osl, Mp, w.eo, w.Ap1, Np, w.ea1, Kp, 1.0, 0.0, reinterpret_cast<double*>(Bc), 1, l);
+    } else {
+      e = prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "sketch");
   }
   const int ldy = pad4(m);
@@ -325,34 +341,43 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
         Tm = w.Tts;
       }
       {
-        // W^T = (Y T)^T A2 ; A2 -= Y W^T  (block reflector: the new R rows and the trailing update of Alg. 4)
-        Phase ph(h, st, RQ_PHASE_TRAILING, 4.0 * mt * (double)n2 * bj + 2.0 * mt * (double)bj * bj,
-                 sz * (3.0 * mt * (double)n2 + 2.0 * bj * (double)n2 + 3.0 * mt * (double)bj));
-        e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, ldy, Tm, b, TS(0), w.YT, ldy);
-        if (w.Ap1) {
+        // W^T = (Y T)^T A2 ; A2 -= Y W^T  (block reflector: the new R rows and the trailing update of Alg. 4).
+        // On the FP64 tensor-core path the operand slicing is timed as its own phase.
+        {
+          Phase ph(h, st, RQ_PHASE_TRAILING, 4.0 * mt * (double)n2 * bj + 2.0 * mt * (double)bj * bj,
+                   sz * (3.0 * mt * (double)n2 + 2.0 * bj * (double)n2 + 3.0 * mt * (double)bj));
+          e = gemm<TS>(c, false, false, mt, bj, bj, TS(1), w.Ybuf, ldy, Tm, b, TS(0), w.YT, ldy);
+          if (e == cudaSuccess && !w.Ap1) e = prod_tn_skinny<TS>(c, bj, n2, mt, w.YT, ldy, A2, lda, w.Wt, b);
+        }
+        if (e == cudaSuccess && w.Ap1) {
           // W = A2^T (Y T) on the tensor cores (FP64 through slices), stored as W^T (bj x n2, ld b)
           const int Mp = oz_rows_pad(n2, true), Np = oz_rows_pad(bj, false), Kp = oz_k_pad(mt);
-          const double* A2d = reinterpret_cast<const double*>(A2);
-          if (e == cudaSuccess) e = oz_slice(c, true, n2, mt, A2d, lda, Mp, Kp, w.Ap1, w.ea1);
-          if (e == cudaSuccess)
-            e = oz_slice(c, true, bj, mt, reinterpret_cast<const double*>(w.YT), ldy, Np, Kp, w.Bp1, w.eb1);
+          {
+            Phase ph(h, st, RQ_PHASE_SLICE, 0.0, 8.0 * ((double)mt * n2 + (double)mt * bj));
+            e = oz_slice(c, true, n2, mt, reinterpret_cast<const double*>(A2), lda, Mp, Kp, w.Ap1, w.ea1);
+            if (e == cudaSuccess)
+              e = oz_slice(c, true, bj, mt, reinterpret_cast<const double*>(w.YT), ldy, Np, Kp, w.Bp1, w.eb1);
+          }
+          Phase ph(h, st, RQ_PHASE_TRAILING, 0.0, 0.0);
           if (e == cudaSuccess)
             e = oz_gemm(c, n2, bj, mt, w.Ap1, Mp, w.ea1, w.Bp1, Np, w.eb1, Kp, 1.0, 0.0,
                         reinterpret_cast<double*>(w.Wt), b, 1);
-        } else if (e == cudaSuccess) {
-          e = prod_tn_skinny<TS>(c, bj, n2, mt, w.YT, ldy, A2, lda, w.Wt, b);
         }
-        if (w.Ap2) {
+        if (e == cudaSuccess && w.Ap2) {
           // A2 -= Y W^T on the tensor cores: operand rows are Y's rows and W^T's columns, K = bj
           const int Mp = oz_rows_pad(mt, true), Np = oz_rows_pad(n2, false), Kp = oz_k_pad(bj);
-          if (e == cudaSuccess)
+          {
+            Phase ph(h, st, RQ_PHASE_SLICE, 0.0, 8.0 * ((double)mt * bj + (double)bj * n2));
             e = oz_slice(c, false, mt, bj, reinterpret_cast<const double*>(w.Ybuf), ldy, Mp, Kp, w.Ap2, w.ea2);
-          if (e == cudaSuccess)
-            e = oz_slice(c, true, n2, bj, reinterpret_cast<const double*>(w.Wt), b, Np, Kp, w.Bp2, w.eb2);
+            if (e == cudaSuccess)
+              e = oz_slice(c, true, n2, bj, reinterpret_cast<const double*>(w.Wt), b, Np, Kp, w.Bp2, w.eb2);
+          }
+          Phase ph(h, st, RQ_PHASE_TRAILING, 0.0, 0.0);
           if (e == cudaSuccess)
             e = oz_gemm(c, mt, n2, bj, w.Ap2, Mp, w.ea2, w.Bp2, Np, w.eb2, Kp, -1.0, 1.0,
                         reinterpret_cast<double*>(A2), 1, lda);
         } else if (e == cudaSuccess) {
+          Phase ph(h, st, RQ_PHASE_TRAILING, 0.0, 0.0);
           e = prod_nn<TS>(c, mt, n2, bj, TS(-1), w.Ybuf, ldy, w.Wt, b, TS(1), A2, lda);
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "trailing update");
