@@ -399,8 +399,19 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
         // B1 -= Omegahat11 R12 with R12 the top bj rows of the updated A2
         if (e == cudaSuccess) {
           if constexpr (sizeof(TS) == sizeof(double)) {
-            e = gemm<TS>(c, false, false, bj, n2, bj, TS(-1), reinterpret_cast<const TS*>(w.Oh), b, A2, lda, TS(1),
-                         Bn, l);
+            if (w.Ap2) {
+              // on the tensor cores: operand rows are Omegahat11's rows and R12's columns, K = bj
+              const int Mp = oz_rows_pad(bj, true), Np = oz_rows_pad(n2, false), Kp = oz_k_pad(bj);
+              e = oz_slice(c, false, bj, bj, w.Oh, b, Mp, Kp, w.Ap2, w.ea2);
+              if (e == cudaSuccess)
+                e = oz_slice(c, true, n2, bj, reinterpret_cast<const double*>(A2), lda, Np, Kp, w.Bp2, w.eb2);
+              if (e == cudaSuccess)
+                e = oz_gemm(c, bj, n2, bj, w.Ap2, Mp, w.ea2, w.Bp2, Np, w.eb2, Kp, -1.0, 1.0,
+                            reinterpret_cast<double*>(Bn), 1, l);
+            } else {
+              e = gemm<TS>(c, false, false, bj, n2, bj, TS(-1), reinterpret_cast<const TS*>(w.Oh), b, A2, lda, TS(1),
+                           Bn, l);
+            }
           } else {
             e = convert<TS, double>(c, bj, bj, w.Oh, b, w.Tts, b);
             if (e == cudaSuccess) e = prod_nn<TS>(c, bj, n2, bj, TS(-1), w.Tts, b, A2, lda, TS(1), Bn, l);
