@@ -269,22 +269,37 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int er = a.ea[row] + a.u - 112;
         double* C = a.C + (size_t)(w / (tiles_m * tiles_n)) * a.czs + (long long)row * a.rs;
         const int col0 = n0 + 32 * h;
-        // C = alpha D + beta C with the common cases (beta 0 or 1, alpha +-1) free of FP64 multiplies
+        // C = alpha D + beta C with the common cases (beta 0 or 1, alpha +-1) free of FP64 multiplies;
+        // every load of C is issued before any store (the stores could otherwise alias the later
+        // loads, which would serialise 32 memory round trips)
         const int mode = a.beta == 0.0 ? (a.alpha == 1.0 ? 0 : 1) : (a.beta == 1.0 && a.alpha == -1.0 ? 2 : 3);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = col0 + j;
-          if (col < a.N) {
-            const double v = f64_from_i64_scaled(acc[j], er + a.eb[col]);
-            double* out = C + (long long)col * a.cs;
-            if (mode == 0)
-              *out = v;
-            else if (mode == 1)
-              *out = a.alpha * v;
-            else if (mode == 2)
-              *out = *out - v;
-            else
-              *out = fma(a.alpha, v, a.beta * *out);
+        for (int j0 = 0; j0 < 32; j0 += 16) {
+          double cv[16];
+          int ebv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) ebv[j] = col0 + j0 + j < a.N ? __ldg(a.eb + col0 + j0 + j) : 0;
+          if (mode >= 2) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              cv[j] = col0 + j0 + j < a.N ? __ldcs(C + (long long)(col0 + j0 + j) * a.cs) : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = col0 + j0 + j;
+            if (col < a.N) {
+              const double v = f64_from_i64_scaled(acc[j0 + j], er + ebv[j]);
+              double r;
+              if (mode == 0)
+                r = v;
+              else if (mode == 1)
+                r = a.alpha * v;
+              else if (mode == 2)
+                r = cv[j] - v;
+              else
+                r = fma(a.alpha, v, a.beta * cv[j]);
+              __stcs(C + (long long)col * a.cs, r);
+            }
           }
         }
       }
