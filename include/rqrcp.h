@@ -152,13 +152,10 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  * sketch serves the truncated paths).  In FP64 the two block reflector
  * products of every block (W^T = (Y T)^T A2 and A2 -= Y W^T) run on the
  * bfloat16 tensor cores through the exact slice split of rq_gemm_f64, which
- * keeps FP64 accuracy, as do the sketch B = Omega A and the product of the
- * sample update; A is read as FP64 and sliced inside the kernel, and the
- * workspace grows by the slices of the b-column operands, about
- * 16 b (m + n) bytes (the environment variable RQ_F64_TC, read when the
- * handle is created, selects "0": every product on the FP64 pipe, "1": only
- * the update A2 -= Y W^T and the sample update on the tensor cores).  rq_qr
- * and rq_rsrqrcp do the same.
+ * keeps FP64 accuracy; the handle's workspace then also holds the slices of
+ * A2, about 16 m n bytes (the environment variable RQ_F64_TC, read when the
+ * handle is created, selects "0": both products on the FP64 pipe, "1": only
+ * the update on the tensor cores).  rq_qr and rq_rsrqrcp do the same.
  */
 int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
              const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
@@ -384,9 +381,8 @@ int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, cons
  * GEMM: below (3 K 2^-53 + 2^-52) 2^(ea_i + eb_j) per entry, with 2^ea_i and
  * 2^eb_j the powers of two just above the largest magnitude of row i of A and
  * column j of B (entries of 2^-1000 or less relative to their row's largest
- * lose accuracy to underflow).  B is read as FP64 and sliced inside the
- * kernel; the handle's workspace holds A's slices, 16 ceil64(M) ceil64(K)
- * bytes, the exponents and FP64 split-K partials.
+ * lose accuracy to underflow).  The handle's workspace holds the slices:
+ * 16 (ceil128(M) + ceil64(N)) ceil64(K) bytes, plus FP64 split-K partials.
  * Errors: -(argument index) for M, N or K < 1, a NULL array or a short
  * leading dimension (h is argument 1); RQ_ENOTIMPL without a tensor-map
  * encoder in the driver.  Asynchronous on stream.

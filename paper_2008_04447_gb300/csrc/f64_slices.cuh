@@ -122,29 +122,6 @@ RQ_HD void f64_add_level(int64_t& acc, float P, int L, int u) {
     acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
 }
 
-// f64_add_level on the bit pattern r of the FP32 partial, with integer
-// operations only (a float -> int conversion runs on the FP64 pipe of GB300):
-// an exact integer |P| < 2^24 is +-M 2^(E - 150) with M the significand and E
-// the biased exponent, so P 2^sh is M shifted by E - 150 + sh, rounded as
-// f64_add_level rounds (half up), bit for bit.
-RQ_HD void f64_add_level_bits(int64_t& acc, uint32_t r, int L, int u) {
-  const int E = static_cast<int>((r >> 23) & 0xffu);
-  if (E == 0) return;                                    // P = 0 (an integer is never subnormal)
-  const int64_t neg = static_cast<int64_t>(r >> 31);
-  const int64_t M = static_cast<int64_t>((r & 0x7fffffu) | 0x800000u);
-  const int s = E - 150 + 112 - kF64SliceBits * L - u;
-  int64_t t;
-  if (s >= 0) {
-    t = M << s;
-  } else if (s > -40) {
-    // (P + 2^(k-1)) >> k for P = +-M 2^-k: half up for both signs
-    t = (M + (static_cast<int64_t>(1) << (-s - 1)) - neg) >> (-s);
-  } else {
-    t = 0;
-  }
-  acc += neg ? -t : t;
-}
-
 RQ_HD double f64_of_bits(uint64_t b) {
 #ifdef __CUDA_ARCH__
   return __longlong_as_double(static_cast<long long>(b));

@@ -83,8 +83,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, u
       : "memory");
 }
 
-// bfloat16 bits of a small integer (|v| <= 127: exact, the low 16 bits of the FP32 value are zero).
-__device__ __forceinline__ uint32_t bf16_bits_of(int v) { return __float_as_uint(static_cast<float>(v)) >> 16; }
+// acc += P 2^sh (sh >= 0) or P 2^sh rounded to nearest (sh < 0): f64_add_level's
+// arithmetic with P, an exact integer below 2^24 held in FP32, converted
+// through int32 (a 32-bit conversion; the 64-bit one runs on the FP64 pipe).
+__device__ __forceinline__ void add_level_fast(int64_t& acc, float P, int sh) {
+  const int64_t p = static_cast<int64_t>(__float2int_rz(P));
+  if (sh >= 0)
+    acc += p << sh;
+  else if (sh > -40)
+    acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
+}
 
 struct OzArgs {
   int M, N, K;              // D = A B^T: A M x K, B N x K
@@ -94,8 +102,6 @@ struct OzArgs {
   int u;                    // accumulator unit exponent, >= f64_acc_unit(K)
   const int* ea;            // M row exponents of A
   const int* eb;            // N row exponents of B
-  const double* Araw;       // RAWA: A's FP64 source, row r's entries at Araw[k + r lda]
-  long long lda;
   double alpha, beta;
   double* C;                // element (i, j) at C[i rs + j cs] (+ z czs for split-K partials)
   long long rs, cs;
@@ -103,16 +109,12 @@ struct OzArgs {
   int* err;
 };
 
-// RAWA: the A operand is read as FP64 (row r's K entries contiguous at
-// Araw + r lda) and cut into slices in shared memory by the drain warps, one
-// or two stages ahead of the MMAs, instead of being loaded as slice planes.
-template <bool RAWA>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  // full[2], empty[2], dfull, ldrained[8], aready[2]
-  __shared__ __align__(8) uint64_t bars[2 * OZ_NS + 1 + OZ_S + OZ_NS];
+  // full[2], empty[2], dfull, ldrained[8]
+  __shared__ __align__(8) uint64_t bars[2 * OZ_NS + 1 + OZ_S];
   __shared__ uint32_t s_tmem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = a.Mp / OZ_BM, tiles_n = a.Np / OZ_BN;
@@ -122,7 +124,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   auto empty = [&](int s) { return bar0 + 8u * (OZ_NS + s); };
   const uint32_t dfull = bar0 + 8u * (2 * OZ_NS);
   auto ldrained = [&](int L) { return bar0 + 8u * (2 * OZ_NS + 1 + L); };
-  auto aready = [&](int s) { return bar0 + 8u * (2 * OZ_NS + 1 + OZ_S + s); };
   auto sA = [&](int s, int i) { return sm + (size_t)s * OZ_STAGE + (size_t)i * OZ_ABYTES; };
   auto sB = [&](int s, int j) { return sm + (size_t)s * OZ_STAGE + OZ_S * OZ_ABYTES + (size_t)j * OZ_BBYTES; };
   // item w -> tile (tm, tn) and K range z (tm fastest)
@@ -144,7 +145,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     mbar_init(dfull, 1);
     for (int L = 0; L < OZ_S; ++L) mbar_init(ldrained(L), 256);
-    for (int s = 0; s < OZ_NS; ++s) mbar_init(aready(s), 256);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -168,11 +168,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int it = 0; it < nk; ++it, ++g) {
           const int s = (int)(g % OZ_NS);
           if (!mbar_wait(empty(s), (uint32_t)((g / OZ_NS) & 1) ^ 1u, a.err)) { ok = false; break; }
-          mbar_expect_tx(full(s), RAWA ? OZ_S * OZ_BBYTES : OZ_STAGE);
+          mbar_expect_tx(full(s), OZ_STAGE);
           const int k = kbeg + it * OZ_BK;
 #pragma unroll 1
           for (int i = 0; i < OZ_S; ++i) {
-            if (!RAWA) tma_load_2d(smem_u32(sA(s, i)), &mapA, k, i * a.Mp + m0, full(s));
+            tma_load_2d(smem_u32(sA(s, i)), &mapA, k, i * a.Mp + m0, full(s));
             tma_load_2d(smem_u32(sB(s, i)), &mapB, k, i * a.Np + n0, full(s));
           }
         }
@@ -194,7 +194,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int s = (int)(g % OZ_NS);
           const int st = it % OZ_STAGES_PER_CHUNK;
           if (!mbar_wait(full(s), (uint32_t)((g / OZ_NS) & 1), a.err)) { ok = false; break; }
-          if (RAWA && !mbar_wait(aready(s), (uint32_t)((g / OZ_NS) & 1), a.err)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
           for (int L = 0; L < OZ_S && ok; ++L) {
@@ -231,57 +230,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int h = (warp - 2) >> 2;    // column half
     long long gc = 0;
     bool ok = true;
-    // RAWA: the slicing cursor (global stage gs = stage its of item ws); warp
-    // w - 2 cuts rows 16 (w - 2) .. 16 (w - 2) + 15 of each stage, lane = k
-    long long gs = 0;
-    int ws = blockIdx.x, its = 0, ws_m0 = 0, ws_kbeg = 0, ws_nk = 0;
-    if (RAWA && ws < items) {
-      int n0x;
-      item(ws, ws_m0, n0x, ws_kbeg, ws_nk);
-    }
-    auto slice_next = [&]() -> bool {
-      const int s = (int)(gs % OZ_NS);
-      if (!mbar_wait(empty(s), (uint32_t)((gs / OZ_NS) & 1) ^ 1u, a.err)) return false;
-      const int r0 = (warp - 2) * 16;
-      const int k = ws_kbeg + its * OZ_BK + lane;
-      const bool kin = k < a.K && k < ws_kbeg + a.kchunk;
-#pragma unroll 1
-      for (int t0 = 0; t0 < 16; t0 += 8) {
-        double x[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int r = ws_m0 + r0 + t0 + t;
-          x[t] = (kin && r < a.M) ? __ldcs(a.Araw + (long long)r * a.lda + k) : 0.0;
-        }
-        // byte offset of (row, k) in a 64-byte-swizzled plane tile: 16-byte chunk (2k / 16) ^ ((row / 2) & 3)
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int row = r0 + t0 + t;
-          const int r = ws_m0 + row;
-          const int ex = r < a.M ? __ldg(a.ea + r) : 0;
-          int sl[OZ_S];
-          f64_slices(x[t], ex, sl);
-          const uint32_t off =
-              (uint32_t)(row * 64 + ((((lane * 2) >> 4) ^ ((row >> 1) & 3)) << 4) + ((lane * 2) & 15));
-#pragma unroll
-          for (int i = 0; i < OZ_S; ++i)
-            *reinterpret_cast<uint16_t*>(sA(s, i) + off) = static_cast<uint16_t>(bf16_bits_of(sl[i]));
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(aready(s));
-      ++gs;
-      if (++its == ws_nk) {
-        its = 0;
-        ws += gridDim.x;
-        if (ws < items) {
-          int n0x;
-          item(ws, ws_m0, n0x, ws_kbeg, ws_nk);
-        }
-      }
-      return true;
-    };
-    long long gstage = 0;  // global index of the first stage of the current item
     for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
       int m0, n0, kbeg, nk;
       item(w, m0, n0, kbeg, nk);
@@ -291,12 +239,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0;
       for (int c = 0; c < nchunks; ++c, ++gc) {
-        if (RAWA) {
-          // slice up to two stages past this chunk's last before draining it
-          const long long gend = gstage + min(nk - 1, c * OZ_STAGES_PER_CHUNK + OZ_STAGES_PER_CHUNK - 1);
-          while (ok && gs <= gend + 2 && ws < items) ok = slice_next();
-          if (!ok) break;
-        }
         if (!mbar_wait(dfull, (uint32_t)(gc & 1), a.err)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -316,12 +258,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // level L is in registers: the next chunk's MMAs may overwrite it
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(ldrained(L));
-          // level L + 2 of f64_add_level, unit 2^u, from the FP32 bit patterns (integer operations only)
+          // level L = 2 + L of f64_add_level, unit 2^u
+          const int sh = 112 - kF64SliceBits * (L + 2) - a.u;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) f64_add_level_bits(acc[j], r[j], L + 2, a.u);
+          for (int j = 0; j < 32; ++j) add_level_fast(acc[j], __uint_as_float(r[j]), sh);
         }
       }
-      gstage += nk;
       if (!ok) break;
       if (row < a.M) {
         const int er = a.ea[row] + a.u - 112;
@@ -371,6 +313,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// bfloat16 bits of a small integer (|v| <= 127: exact, the low 16 bits of the FP32 value are zero).
+__device__ __forceinline__ uint32_t bf16_bits_of(int v) { return __float_as_uint(static_cast<float>(v)) >> 16; }
 
 // Operand rows are source COLUMNS: row r's K entries are src[k + r ld] (contiguous).
 // One warp per row: the largest magnitude (compared as bit patterns), its exponent,
@@ -476,33 +420,6 @@ __global__ void slice_rows_kernel(int R, int K, const double* __restrict__ src, 
   }
 }
 
-// The exponent of each operand row whose K entries are a source column
-// (src[k + r ld]): one 256-thread CTA per row, the largest magnitude compared
-// as bit patterns.
-__global__ void __launch_bounds__(256) exp_cols_kernel(int R, int K, const double* __restrict__ src, long long ld,
-                                                       int* __restrict__ e) {
-  __shared__ unsigned long long s_mx[8];
-  const int r = blockIdx.x, t = threadIdx.x;
-  const double* col = src + (long long)r * ld;
-  unsigned long long mx = 0;
-  for (int k = t; k < K; k += 256) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldcs(col + k))) & 0x7fffffffffffffffull;
-    mx = b > mx ? b : mx;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = y > mx ? y : mx;
-  }
-  if ((t & 31) == 0) s_mx[t >> 5] = mx;
-  __syncthreads();
-  if (t == 0) {
-    for (int w = 1; w < 8; ++w) mx = s_mx[w] > mx ? s_mx[w] : mx;
-    mx = s_mx[0] > mx ? s_mx[0] : mx;
-    e[r] = f64_scale_exponent(__longlong_as_double(static_cast<long long>(mx)));
-  }
-}
-
 // C = alpha sum_z P_z + beta C over the split-K partials (P_z compact, M x N
 // column-major), C element (i, j) at C[i rs + j cs].
 __global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__ P, size_t pzs, double alpha,
@@ -553,16 +470,11 @@ cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const dou
   return cudaGetLastError();
 }
 
-namespace {
-cudaError_t oz_gemm_any(const Ctx& c, int M, int N, int K, const uint16_t* Ap, const double* Araw, long long lda, int Mp,
-                        const int* ea, const uint16_t* Bp, int Np, const int* eb, int Kp, double alpha, double beta,
-                        double* C, long long rs, long long cs) {
+cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int Mp, const int* ea, const uint16_t* Bp,
+                    int Np, const int* eb, int Kp, double alpha, double beta, double* C, long long rs, long long cs) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   CUtensorMap ma, mb;
-  if (!make_plane_map(&mb, Bp, Kp, OZ_S * Np, OZ_BN)) return cudaErrorInvalidValue;
-  if (Araw)
-    ma = mb;  // unused in the raw mode
-  else if (!make_plane_map(&ma, Ap, Kp, OZ_S * Mp, OZ_BM))
+  if (!make_plane_map(&ma, Ap, Kp, OZ_S * Mp, OZ_BM) || !make_plane_map(&mb, Bp, Kp, OZ_S * Np, OZ_BN))
     return cudaErrorInvalidValue;
   const int tiles = (Mp / OZ_BM) * (Np / OZ_BN);
   // split K when the tiles do not fill the GPU (chunks of whole drains, partials in FP64)
@@ -591,8 +503,6 @@ cudaError_t oz_gemm_any(const Ctx& c, int M, int N, int K, const uint16_t* Ap, c
   args.u = f64_acc_unit(K);
   args.ea = ea;
   args.eb = eb;
-  args.Araw = Araw;
-  args.lda = lda;
   args.err = c.err;
   if (S == 1) {
     args.alpha = alpha;
@@ -610,15 +520,11 @@ cudaError_t oz_gemm_any(const Ctx& c, int M, int N, int K, const uint16_t* Ap, c
     args.czs = (size_t)M * N;
   }
   const size_t smem = oz_smem();
-  const void* fn = Araw ? (const void*)oz_gemm_kernel<true> : (const void*)oz_gemm_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int items = tiles * S;
   const int grid = items < c.num_sms ? items : c.num_sms;
-  if (Araw)
-    oz_gemm_kernel<true><<<grid, OZ_THREADS, smem, c.stream>>>(ma, mb, args);
-  else
-    oz_gemm_kernel<false><<<grid, OZ_THREADS, smem, c.stream>>>(ma, mb, args);
+  oz_gemm_kernel<<<grid, OZ_THREADS, smem, c.stream>>>(ma, mb, args);
   ++*c.launches;
   e = cudaGetLastError();
   if (e != cudaSuccess || S == 1) return e;
@@ -627,25 +533,6 @@ cudaError_t oz_gemm_any(const Ctx& c, int M, int N, int K, const uint16_t* Ap, c
   if (blocks > 8 * c.num_sms) blocks = 8 * c.num_sms;
   oz_reduce_kernel<<<blocks, 256, 0, c.stream>>>(M, N, S, static_cast<const double*>(c.splitk), total, alpha, beta, C,
                                                  rs, cs);
-  ++*c.launches;
-  return cudaGetLastError();
-}
-}  // namespace
-
-cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int Mp, const int* ea, const uint16_t* Bp,
-                    int Np, const int* eb, int Kp, double alpha, double beta, double* C, long long rs, long long cs) {
-  return oz_gemm_any(c, M, N, K, Ap, nullptr, 0, Mp, ea, Bp, Np, eb, Kp, alpha, beta, C, rs, cs);
-}
-
-cudaError_t oz_gemm_raw(const Ctx& c, int M, int N, int K, const double* A, long long lda, const int* ea,
-                        const uint16_t* Bp, int Np, const int* eb, int Kp, double alpha, double beta, double* C,
-                        long long rs, long long cs) {
-  return oz_gemm_any(c, M, N, K, nullptr, A, lda, oz_rows_pad(M, true), ea, Bp, Np, eb, Kp, alpha, beta, C, rs, cs);
-}
-
-cudaError_t oz_exponents(const Ctx& c, int R, int K, const double* src, long long ld, int* e) {
-  if (R <= 0) return cudaSuccess;
-  exp_cols_kernel<<<R, 256, 0, c.stream>>>(R, K, src, ld, e);
   ++*c.launches;
   return cudaGetLastError();
 }

@@ -156,12 +156,6 @@ cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const dou
                      uint16_t* planes, int* e);
 cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int Mp, const int* ea, const uint16_t* Bp,
                     int Np, const int* eb, int Kp, double alpha, double beta, double* C, long long rs, long long cs);
-// The same with A read as FP64 (row r's K entries at A[k + r lda]) and sliced in
-// shared memory inside the kernel; ea must hold oz_exponents of those rows.
-cudaError_t oz_gemm_raw(const Ctx& c, int M, int N, int K, const double* A, long long lda, const int* ea,
-                        const uint16_t* Bp, int Np, const int* eb, int Kp, double alpha, double beta, double* C,
-                        long long rs, long long cs);
-cudaError_t oz_exponents(const Ctx& c, int R, int K, const double* src, long long ld, int* e);
 
 // Blocked Householder QR (Alg. 4 with pivot, unpivoted without) over a
 // caller-provided workspace of factor_ws_bytes bytes; h may be NULL.  Shared by

@@ -127,16 +127,14 @@ struct OzWs {
   size_t split_bytes;
 };
 
-// (the A operand's slice planes, Mp rows; only the exponents of B's Nr rows,
-// which the product reads as FP64)
-OzWs carve_oz(Carver& cv, int Mp, int Nr, int Kp, size_t mn) {
+OzWs carve_oz(Carver& cv, int Mp, int Np, int Kp, size_t mn) {
   OzWs z;
   z.bar = cv.take<unsigned int>(4);
   z.err = reinterpret_cast<int*>(z.bar + 2);
   z.Ap = cv.take<uint16_t>(oz_plane_bytes(Mp, Kp) / 2);
-  z.Bp = nullptr;
+  z.Bp = cv.take<uint16_t>(oz_plane_bytes(Np, Kp) / 2);
   z.ea = cv.take<int>(Mp);
-  z.eb = cv.take<int>(Nr);
+  z.eb = cv.take<int>(Np);
   const int chunks = (Kp + 127) / 128;
   z.split_bytes = (size_t)(chunks < 16 ? chunks : 16) * sizeof(double) * mn;
   z.split = cv.take<char>(z.split_bytes);
@@ -206,11 +204,9 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
     w.Bp2 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(n, false), kb) / 2);
     w.eb2 = c.take<int>(oz_rows_pad(n, false));
     if (f64tc > 1) {
-      // W = A2^T (Y T) and the sketch read A2 / A as FP64 and slice them in the kernel:
-      // only their column exponents are stored (Ap1 marks the mode)
       const int km = oz_k_pad(m);
+      w.Ap1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(n, true), km) / 2);
       w.ea1 = c.take<int>(oz_rows_pad(n, true));
-      w.Ap1 = reinterpret_cast<uint16_t*>(w.ea1);
       w.Bp1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(b, false), km) / 2);
       w.eb1 = c.take<int>(oz_rows_pad(b, false));
       if (l > 1 && !resample) {
@@ -301,15 +297,13 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
     // Alg. 4: B = Omega A
     Phase ph(h, st, RQ_PHASE_SKETCH, 2.0 * l * (double)m * n, sz * ((double)m * n + (double)l * m + (double)l * n));
     if (w.Osl) {
-      // FP64 B = Omega A on the tensor cores, as B^T = A^T Omega^T: operand rows are A's columns (read
-      // as FP64 and sliced inside the product) and Omega's rows, K = m
-      const int Np = oz_rows_pad(l, false), Kp = oz_k_pad(m);
-      const double* Ad = reinterpret_cast<const double*>(A);
-      e = oz_exponents(c, n, m, Ad, lda, w.ea1);
+      // FP64 B = Omega A on the tensor cores: operand rows are Omega's rows and A's columns, K = m
+      const int Mp = oz_rows_pad(l, true), Np = oz_rows_pad(n, false), Kp = oz_k_pad(m);
+      e = oz_slice(c, false, l, m, reinterpret_cast<const double*>(Omega), ldo, Mp, Kp, w.Osl, w.eo);
       if (e == cudaSuccess)
-        e = oz_slice(c, false, l, m, reinterpret_cast<const double*>(Omega), ldo, Np, Kp, w.Osl, w.eo);
+        e = oz_slice(c, true, n, m, reinterpret_cast<const double*>(A), lda, Np, Kp, w.Ap1, w.ea1);
       if (e == cudaSuccess)
-        e = oz_gemm_raw(c, n, l, m, Ad, lda, w.ea1, w.Osl, Np, w.eo, Kp, 1.0, 0.0, reinterpret_cast<double*>(Bc), l, 1);
+        e = oz_gemm(c, l, n, m, w.Osl, Mp, w.eo, w.Ap1, Np, w.ea1, Kp, 1.0, 0.0, reinterpret_cast<double*>(Bc), 1, l);
     } else {
       e = prod_nn<TS>(c, l, n, m, TS(1), Omega, ldo, A, lda, TS(0), Bc, l);
     }
@@ -357,19 +351,17 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
         }
         if (e == cudaSuccess && w.Ap1) {
           // W = A2^T (Y T) on the tensor cores (FP64 through slices), stored as W^T (bj x n2, ld b)
-          // (A2 is read as FP64 and sliced inside the product; only its column exponents are formed first)
-          const int Np = oz_rows_pad(bj, false), Kp = oz_k_pad(mt);
-          const double* A2d = reinterpret_cast<const double*>(A2);
+          const int Mp = oz_rows_pad(n2, true), Np = oz_rows_pad(bj, false), Kp = oz_k_pad(mt);
           {
             Phase ph(h, st, RQ_PHASE_SLICE, 0.0, 8.0 * ((double)mt * n2 + (double)mt * bj));
-            e = oz_exponents(c, n2, mt, A2d, lda, w.ea1);
+            e = oz_slice(c, true, n2, mt, reinterpret_cast<const double*>(A2), lda, Mp, Kp, w.Ap1, w.ea1);
             if (e == cudaSuccess)
               e = oz_slice(c, true, bj, mt, reinterpret_cast<const double*>(w.YT), ldy, Np, Kp, w.Bp1, w.eb1);
           }
           Phase ph(h, st, RQ_PHASE_TRAILING, 0.0, 0.0);
           if (e == cudaSuccess)
-            e = oz_gemm_raw(c, n2, bj, mt, A2d, lda, w.ea1, w.Bp1, Np, w.eb1, Kp, 1.0, 0.0,
-                            reinterpret_cast<double*>(w.Wt), b, 1);
+            e = oz_gemm(c, n2, bj, mt, w.Ap1, Mp, w.ea1, w.Bp1, Np, w.eb1, Kp, 1.0, 0.0,
+                        reinterpret_cast<double*>(w.Wt), b, 1);
         }
         if (e == cudaSuccess && w.Ap2) {
           // A2 -= Y W^T on the tensor cores: operand rows are Y's rows and W^T's columns, K = bj
@@ -1290,23 +1282,21 @@ int rq_gemm_f64(rq_handle h, int M, int N, int K, const double* A, int lda, cons
   }
   if (!oz_supported()) return fail(h, RQ_ENOTIMPL, "rq_gemm_f64: no tensor-map encoder in this driver");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // as C^T = B^T A^T: the product's rows are B's columns (read as FP64, K contiguous), its
-  // columns A's rows (sliced into planes first); C (i, j) = D (j, i)
-  const int Mp = oz_rows_pad(M, false), Kp = oz_k_pad(K);
+  const int Mp = oz_rows_pad(M, true), Np = oz_rows_pad(N, false), Kp = oz_k_pad(K);
   Carver cv(nullptr);
-  OzWs z = carve_oz(cv, Mp, N, Kp, (size_t)M * N);
+  OzWs z = carve_oz(cv, Mp, Np, Kp, (size_t)M * N);
   const int rc = ensure_ws(h, align_up(cv.off, 256));
   if (rc) return rc;
   Carver cw(h->ws);
-  z = carve_oz(cw, Mp, N, Kp, (size_t)M * N);
+  z = carve_oz(cw, Mp, Np, Kp, (size_t)M * N);
   Ctx c{st, h->num_sms, &h->launches, z.err, z.bar, z.split, z.split_bytes};
   cudaError_t e;
   {
     Phase ph(h, st, RQ_PHASE_OTHER, 2.0 * M * N * (double)K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
     e = cudaMemsetAsync(z.bar, 0, 16, st);
     if (e == cudaSuccess) e = oz_slice(c, false, M, K, A, lda, Mp, Kp, z.Ap, z.ea);
-    if (e == cudaSuccess) e = oz_exponents(c, N, K, B, ldb, z.eb);
-    if (e == cudaSuccess) e = oz_gemm_raw(c, N, M, K, B, ldb, z.eb, z.Ap, Mp, z.ea, Kp, 1.0, 0.0, C, ldc, 1);
+    if (e == cudaSuccess) e = oz_slice(c, true, N, K, B, ldb, Np, Kp, z.Bp, z.eb);
+    if (e == cudaSuccess) e = oz_gemm(c, M, N, K, z.Ap, Mp, z.ea, z.Bp, Np, z.eb, Kp, 1.0, 0.0, C, 1, ldc);
     if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, z.err, sizeof(int), cudaMemcpyDeviceToDevice, st);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "rq_gemm_f64");
