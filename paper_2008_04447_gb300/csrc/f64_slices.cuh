@@ -104,17 +104,6 @@ RQ_HD void f64_slices(double x, int e, int s[kF64Slices]) {
   }
 }
 
-// bfloat16 bits of a slice v (|v| <= 127: exact), built with integer
-// operations (an int -> float conversion runs on GB300's slow conversion
-// pipe): sign, biased exponent 127 + e of the leading bit e, and the 7 bits
-// below it.
-RQ_HD uint32_t f64_slice_bf16_bits(int v) {
-  if (v == 0) return 0u;
-  const uint32_t m = static_cast<uint32_t>(v < 0 ? -v : v);
-  const int e = 63 - clz64(m);
-  return (v < 0 ? 0x8000u : 0u) | (static_cast<uint32_t>(127 + e) << 7) | ((m << (7 - e)) & 0x7fu);
-}
-
 // u = 50 + ceil(log2 K): the accumulator's unit exponent for a K-term product.
 RQ_HD int f64_acc_unit(int K) {
   int c = 0;
@@ -131,29 +120,6 @@ RQ_HD void f64_add_level(int64_t& acc, float P, int L, int u) {
     acc += p * (static_cast<int64_t>(1) << sh);
   else if (sh > -40)                             // |p| < 2^24: a shift of 40 or more leaves 0
     acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
-}
-
-// f64_add_level on the bit pattern r of the FP32 partial, with integer
-// operations only (a float -> int conversion runs on the FP64 pipe of GB300):
-// an exact integer |P| < 2^24 is +-M 2^(E - 150) with M the significand and E
-// the biased exponent, so P 2^sh is M shifted by E - 150 + sh, rounded as
-// f64_add_level rounds (half up), bit for bit.
-RQ_HD void f64_add_level_bits(int64_t& acc, uint32_t r, int L, int u) {
-  const int E = static_cast<int>((r >> 23) & 0xffu);
-  if (E == 0) return;                                    // P = 0 (an integer is never subnormal)
-  const int64_t neg = static_cast<int64_t>(r >> 31);
-  const int64_t M = static_cast<int64_t>((r & 0x7fffffu) | 0x800000u);
-  const int s = E - 150 + 112 - kF64SliceBits * L - u;
-  int64_t t;
-  if (s >= 0) {
-    t = M << s;
-  } else if (s > -40) {
-    // (P + 2^(k-1)) >> k for P = +-M 2^-k: half up for both signs
-    t = (M + (static_cast<int64_t>(1) << (-s - 1)) - neg) >> (-s);
-  } else {
-    t = 0;
-  }
-  acc += neg ? -t : t;
 }
 
 RQ_HD double f64_of_bits(uint64_t b) {

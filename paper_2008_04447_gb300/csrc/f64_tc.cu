@@ -83,6 +83,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, u
       : "memory");
 }
 
+// acc += P 2^sh (sh >= 0) or P 2^sh rounded to nearest (sh < 0): f64_add_level's
+// arithmetic with P, an exact integer below 2^24 held in FP32, converted
+// through int32 (a 32-bit conversion; the 64-bit one runs on the FP64 pipe).
+__device__ __forceinline__ void add_level_fast(int64_t& acc, float P, int sh) {
+  const int64_t p = static_cast<int64_t>(__float2int_rz(P));
+  if (sh >= 0)
+    acc += p << sh;
+  else if (sh > -40)
+    acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
+}
+
 struct OzArgs {
   int M, N, K;              // D = A B^T: A M x K, B N x K
   int Mp, Np;               // plane row counts (the row offset of plane s is s Mp, s Np)
@@ -247,9 +258,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // level L is in registers: the next chunk's MMAs may overwrite it
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(ldrained(L));
-          // level L + 2 of f64_add_level, unit 2^u, from the FP32 bit patterns (integer operations only)
+          // level L = 2 + L of f64_add_level, unit 2^u
+          const int sh = 112 - kF64SliceBits * (L + 2) - a.u;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) f64_add_level_bits(acc[j], r[j], L + 2, a.u);
+          for (int j = 0; j < 32; ++j) add_level_fast(acc[j], __uint_as_float(r[j]), sh);
         }
       }
       if (!ok) break;
@@ -301,6 +313,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// bfloat16 bits of a small integer (|v| <= 127: exact, the low 16 bits of the FP32 value are zero).
+__device__ __forceinline__ uint32_t bf16_bits_of(int v) { return __float_as_uint(static_cast<float>(v)) >> 16; }
 
 // Operand rows are source COLUMNS: row r's K entries are src[k + r ld] (contiguous).
 // One warp per row: the largest magnitude (compared as bit patterns), its exponent,
@@ -331,7 +345,7 @@ __global__ void slice_cols_kernel(int R, int K, const double* __restrict__ src, 
     int s[OZ_S];
     f64_slices(x, ex, s);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(f64_slice_bf16_bits(s[i]));
+    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(bf16_bits_of(s[i]));
   }
 }
 
@@ -368,7 +382,7 @@ __global__ void __launch_bounds__(256) slice_cols_long_kernel(int R, int K, cons
     int s[OZ_S];
     f64_slices(x, ex, s);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(f64_slice_bf16_bits(s[i]));
+    for (int i = 0; i < OZ_S; ++i) out[i * pstride + k] = static_cast<uint16_t>(bf16_bits_of(s[i]));
   }
 }
 
@@ -398,7 +412,7 @@ __global__ void slice_rows_kernel(int R, int K, const double* __restrict__ src, 
       f64_slices((r < R && k < K) ? src[r + (long long)k * ld] : 0.0, ex, s0);
       f64_slices((r < R && k + 1 < K) ? src[r + (long long)(k + 1) * ld] : 0.0, ex, s1);
 #pragma unroll
-      for (int i = 0; i < OZ_S; ++i) w[i][t / 2] = f64_slice_bf16_bits(s0[i]) | (f64_slice_bf16_bits(s1[i]) << 16);
+      for (int i = 0; i < OZ_S; ++i) w[i][t / 2] = bf16_bits_of(s0[i]) | (bf16_bits_of(s1[i]) << 16);
     }
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i)

@@ -28,24 +28,6 @@ long long f64s_combine(const float* P, int nchunks, int u) {
 
 double f64s_from_acc(long long acc, int u, int ea, int eb) { return rq::f64_from_acc(acc, u, ea, eb); }
 
-// acc after adding each P[i] at level L[i], unit u[i], from 0: by f64_add_level
-// (out_a) and by f64_add_level_bits on the FP32 bit pattern (out_b).
-void f64s_add_level_pair(const float* P, const int* L, const int* u, int n, long long* out_a, long long* out_b) {
-  for (int i = 0; i < n; ++i) {
-    int64_t a = 0, b = 0;
-    rq::f64_add_level(a, P[i], L[i], u[i]);
-    uint32_t bits;
-    std::memcpy(&bits, &P[i], sizeof bits);
-    rq::f64_add_level_bits(b, bits, L[i], u[i]);
-    out_a[i] = a;
-    out_b[i] = b;
-  }
-}
-
-void f64s_slice_bf16_bits(const int* v, int n, unsigned* out) {
-  for (int i = 0; i < n; ++i) out[i] = rq::f64_slice_bf16_bits(v[i]);
-}
-
 void f64s_from_i64_scaled(const long long* acc, const int* ex, int n, double* out) {
   for (int i = 0; i < n; ++i) out[i] = rq::f64_from_i64_scaled(acc[i], ex[i]);
 }

@@ -41,8 +41,6 @@ def lib(tmp_path_factory):
     L.f64s_from_acc.argtypes = [ctypes.c_longlong, I, I, I]
     L.f64s_from_acc.restype = ctypes.c_double
     L.f64s_from_i64_scaled.argtypes = [P, P, I, P]
-    L.f64s_add_level_pair.argtypes = [P, P, P, I, P, P]
-    L.f64s_slice_bf16_bits.argtypes = [P, I, P]
     return L
 
 
@@ -164,34 +162,6 @@ def test_integer_conversion_equals_rounded_conversion(lib):
     for a, e, o in zip(acc, ex, out):
         want = float(Fraction(int(a)) * Fraction(2) ** int(e))   # Fraction -> float rounds half to even
         assert o == want, (int(a), int(e), o, want)
-
-
-def test_slice_bfloat16_bits_equal_the_rounded_value(lib):
-    """Every slice value |v| <= 127 gets the bfloat16 bit pattern of v (the top
-    16 bits of its FP32 pattern, exact since v has at most 7 significant bits)."""
-    v = np.arange(-127, 128, dtype=np.int32)
-    out = np.empty(v.size, dtype=np.uint32)
-    lib.f64s_slice_bf16_bits(_ptr(v), v.size, _ptr(out))
-    want = v.astype(np.float32).view(np.uint32) >> 16
-    assert np.array_equal(out, want)
-
-
-def test_level_add_from_bits_equals_the_conversion(lib):
-    """f64_add_level_bits (integer operations on the FP32 bit pattern, the device
-    drain's form) adds exactly what f64_add_level adds, rounding ties included,
-    for exact integer partials |P| < 2^24 at every level and unit."""
-    g = np.random.default_rng(7)
-    n = 20000
-    P = np.concatenate([g.integers(-(2 ** 24) + 1, 2 ** 24, n // 2),
-                        g.integers(-300, 300, n // 4),
-                        (g.integers(-(2 ** 10), 2 ** 10, n // 4) * 2 ** g.integers(0, 14, n // 4))])
-    P = np.clip(P, -(2 ** 24) + 1, 2 ** 24 - 1).astype(np.float32)
-    L = g.integers(2, 10, P.size).astype(np.int32)
-    u = g.integers(50, 67, P.size).astype(np.int32)
-    out_a = np.empty(P.size, dtype=np.int64)
-    out_b = np.empty(P.size, dtype=np.int64)
-    lib.f64s_add_level_pair(_ptr(P), _ptr(L), _ptr(u), P.size, _ptr(out_a), _ptr(out_b))
-    assert np.array_equal(out_a, out_b), int(np.nonzero(out_a != out_b)[0][0])
 
 
 def test_header_compiles_for_the_device(tmp_path):
