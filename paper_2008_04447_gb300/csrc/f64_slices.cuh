@@ -122,42 +122,6 @@ RQ_HD void f64_add_level(int64_t& acc, float P, int L, int u) {
     acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
 }
 
-RQ_HD double f64_of_bits(uint64_t b) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double(static_cast<long long>(b));
-#else
-  double x;
-  std::memcpy(&x, &b, sizeof x);
-  return x;
-#endif
-}
-
-// acc 2^ex as FP64, rounded to nearest even, with integer operations only (on
-// GB300 an int64 -> FP64 conversion runs on the FP64 pipe, which issues about
-// two operations per clock per SM): the leading bit gives the exponent, the 53
-// bits below it the significand, the bits dropped the rounding.  Results
-// outside the normal range take the conversion and ldexp.  Equal, bit for
-// bit, to f64_from_acc's ldexp((double)acc, ex) in the normal range.
-RQ_HD double f64_from_i64_scaled(int64_t acc, int ex) {
-  if (acc == 0) return 0.0;
-  const uint64_t sign = acc < 0 ? 0x8000000000000000ull : 0ull;
-  const uint64_t mag = acc < 0 ? 0ull - static_cast<uint64_t>(acc) : static_cast<uint64_t>(acc);
-  const int lz = clz64(mag);
-  int e = 63 - lz + ex;                          // exponent of the leading bit
-  const uint64_t nrm = mag << lz;                // leading 1 at bit 63
-  uint64_t m = nrm >> 11;                        // 53 bits
-  const uint64_t rem = nrm & 0x7ffull;
-  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) {
-    ++m;
-    if (m == (1ull << 53)) {
-      m >>= 1;
-      ++e;
-    }
-  }
-  if (e < -1022 || e > 1023) return ldexp(static_cast<double>(acc), ex);
-  return f64_of_bits(sign | (static_cast<uint64_t>(e + 1023) << 52) | (m & ((1ull << 52) - 1)));
-}
-
 // The FP64 value of acc (units 2^u) for row and column exponents ea, eb: one
 // rounding (int64 to FP64), then an exact power-of-two scaling.
 RQ_HD double f64_from_acc(int64_t acc, int u, int ea, int eb) {

@@ -94,6 +94,15 @@ __device__ __forceinline__ void add_level_fast(int64_t& acc, float P, int sh) {
     acc += (p + (static_cast<int64_t>(1) << (-sh - 1))) >> (-sh);
 }
 
+// v 2^ex, exactly: the exponent field moves when v and the result are normal,
+// else ldexp.
+__device__ __forceinline__ double scale_pow2(double v, int ex) {
+  const long long b = __double_as_longlong(v);
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  if (E > 0 && E + ex > 0 && E + ex < 2047) return __longlong_as_double(b + (static_cast<long long>(ex) << 52));
+  return v == 0.0 ? v : ldexp(v, ex);
+}
+
 struct OzArgs {
   int M, N, K;              // D = A B^T: A M x K, B N x K
   int Mp, Np;               // plane row counts (the row offset of plane s is s Mp, s Np)
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int j = 0; j < 16; ++j) {
             const int col = col0 + j0 + j;
             if (col < a.N) {
-              const double v = f64_from_i64_scaled(acc[j0 + j], er + ebv[j]);
+              const double v = scale_pow2(static_cast<double>(acc[j0 + j]), er + ebv[j]);
               double r;
               if (mode == 0)
                 r = v;

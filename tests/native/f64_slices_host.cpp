@@ -28,8 +28,5 @@ long long f64s_combine(const float* P, int nchunks, int u) {
 
 double f64s_from_acc(long long acc, int u, int ea, int eb) { return rq::f64_from_acc(acc, u, ea, eb); }
 
-void f64s_from_i64_scaled(const long long* acc, const int* ex, int n, double* out) {
-  for (int i = 0; i < n; ++i) out[i] = rq::f64_from_i64_scaled(acc[i], ex[i]);
-}
 
 }  // extern "C"
