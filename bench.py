@@ -156,6 +156,20 @@ def bf16_peak_tflops():
     return 1700.0, "fallback: 1.7 PFLOP/s, an earlier sustained GB300 bf16 measurement"
 
 
+# DRAM bytes per trailing entry (m_t n2 of a block) moved by the two FP64
+# tensor-core products, from the ncu capture of a 6144 x 6144 factorisation
+# summarised in profiles/oz_gemm_fp64_6144_ncu.md: W = A2^T (Y T) reads A2's
+# slice planes once (1.03 x 16 B) and the update reads and writes A2
+# (0.91 x 16 B).  Valid while those kernels are unchanged.
+OZ_DRAM_BYTES_PER_ENTRY = 16.0 * (1.03 + 0.91)
+
+
+def trailing_entries(m, n, b, k=None):
+    """sum over blocks of m_t n2: the entries the trailing update touches."""
+    k = min(m, n) if k is None else k
+    return sum(float(m - j0) * (n - j0 - min(b, k - j0)) for j0 in range(0, k, b))
+
+
 def slice_pair_flops(m, n, b, k=None):
     """bfloat16 tensor-core flops of the FP64 trailing update through slices:
     36 slice-pair products for each of the two block reflector products
@@ -863,7 +877,9 @@ def main():
         pk, pk_src = bf16_peak_tflops()
         tc_rate = slice_pair_flops(m, n, b) * args.steps / (tr[0] / 1e3) / 1e12
         roofline = {"bound": "tensor", "achieved": tc_rate, "peak": pk, "unit": "TFLOP/s", "frac": tc_rate / pk,
-                    "traffic": None,
+                    "traffic": OZ_DRAM_BYTES_PER_ENTRY * trailing_entries(m, n, b),
+                    "traffic_scope": "DRAM bytes per step of the two tensor-core products (W and the update), "
+                                     "scaled by m_t n2 from an ncu capture of a 6144^2 factorisation",
                     "kernel": "trailing update: oz_gemm_kernel (FP64 block reflector products as 36 bfloat16 "
                               "slice-pair MMAs) + the Y T product; operand slicing is its own phase",
                     "achieved_is": "bfloat16 slice-pair flops per second over the trailing phase's CUDA-event time",

@@ -30,3 +30,16 @@ def test_cpu_context_times_the_oracle_and_lapack():
     assert out["cores"] >= 1
     for key in ("oracle_tuxv_200x120_k8_s", "lapack_dgeqrf_64_s", "lapack_dgeqp3_64_s"):
         assert out[key] > 0.0
+
+
+def test_trailing_counts():
+    """The trailing update touches sum_J m_t n2 entries (about n^3 / (3 b) for a
+    square matrix), and its tensor-core flops are 36 slice pairs of the two
+    2 m_t n2 b_J products."""
+    import bench
+    n, b = 4096, 64
+    ent = bench.trailing_entries(n, n, b)
+    assert abs(ent / (n ** 3 / (3 * b)) - 1) < 0.03
+    assert bench.trailing_entries(100, 50, 64) == 100 * (50 - 50)  # one block covers every column
+    fl = bench.slice_pair_flops(n, n, b)
+    assert abs(fl - 36 * 4 * b * ent) / fl < 1e-12
