@@ -28,7 +28,7 @@ constexpr int kMaxLB = 128;  // largest sample rank of the batched path
 // Dynamic shared memory per CTA: the block GEMM's tiles, or (at other times)
 // the live sample or the current panel when they fit, so that the serial
 // pivot / reflector steps run out of shared memory instead of L2.
-constexpr int kStageFloats = 50 * 1024;  // 200 KB
+constexpr int kStageFloats = 27 * 1024;  // 108 KB: two CTAs per SM
 constexpr int kMaxDevices = 64;
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -783,7 +783,7 @@ __device__ void core_svd_b(const rq_problem& pr, Slot& w, float* sm) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) tuxv_batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NT, 2) tuxv_batched_kernel(BatchArgs a) {
   extern __shared__ float sm[];
   __shared__ Shm s;
   __shared__ int s_idx;

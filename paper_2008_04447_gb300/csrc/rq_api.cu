@@ -209,7 +209,7 @@ FactorWs<TS> carve_factor(void* base, int m, int n, int b, int l, int num_sms, b
       w.ea1 = c.take<int>(oz_rows_pad(n, true));
       w.Bp1 = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(b, false), km) / 2);
       w.eb1 = c.take<int>(oz_rows_pad(b, false));
-      if (l > 1 && !resample) {
+      if (l > 1) {
         w.Osl = c.take<uint16_t>(oz_plane_bytes(oz_rows_pad(l, true), km) / 2);
         w.eo = c.take<int>(oz_rows_pad(l, true));
       }
@@ -388,8 +388,19 @@ int factor_blocks(rq_handle h, void* ws, int num_sms, long long* launches, bool 
         Phase ph(h, st, RQ_PHASE_SAMPLE_UPDATE, 2.0 * l * (double)m2 * n2,
                  sz * ((double)m2 * n2 + 2.0 * l * (double)m2 + (double)l * n2));
         e = gaussian<TS>(c, *rs_seed, (uint64_t)(j0 / b + 1), l, m2, w.Om, l);
-        if (e == cudaSuccess)
+        if (w.Osl && m2 > 0) {
+          // FP64 on the tensor cores: operand rows are the draws' rows and the trailing columns, K = m2
+          const int Mp = oz_rows_pad(l, true), Np = oz_rows_pad(n2, false), Kp = oz_k_pad(m2);
+          if (e == cudaSuccess)
+            e = oz_slice(c, false, l, m2, reinterpret_cast<const double*>(w.Om), l, Mp, Kp, w.Osl, w.eo);
+          if (e == cudaSuccess)
+            e = oz_slice(c, true, n2, m2, reinterpret_cast<const double*>(A2 + bj), lda, Np, Kp, w.Ap1, w.ea1);
+          if (e == cudaSuccess)
+            e = oz_gemm(c, l, n2, m2, w.Osl, Mp, w.eo, w.Ap1, Np, w.ea1, Kp, 1.0, 0.0, reinterpret_cast<double*>(Bn),
+                        1, l);
+        } else if (e == cudaSuccess) {
           e = prod_nn<TS>(c, l, n2, m2, TS(1), w.Om, l, A2 + bj, lda, TS(0), Bn, l);
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "resample");
       } else if (pivot && j0 + bj < k) {
         // Eq. (update1): B1 = S12 - (S11 R11^{-1}) R12, B2 = S22
