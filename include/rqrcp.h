@@ -172,17 +172,19 @@ int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p
  * RQ_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
  * loads the library holds until the process exits.  It keeps fewer split-K
  * partial copies of the W^T product than a handle (none in FP64, four in
- * FP32), so FP64 results equal rq_rqrcp's to rounding and FP32 results agree
- * within the FP32 path's tolerances (the products may be cut into different
- * inner-dimension chunks), not bit for bit.  Its scratch, with s the element
+ * FP32) and runs the FP64 products on the FP64 pipe (rq_rqrcp's tensor-core
+ * slices would not fit the array), so FP64 results equal rq_rqrcp's to
+ * rounding and FP32 results agree within the FP32 path's tolerances (the
+ * products may be cut into different inner-dimension chunks), not bit for
+ * bit.  Its scratch, with s the element
  * size (8 FP64, 4 FP32), G the device's SM count and every term rounded up to
  * 256 bytes, is
  *   s (2 l n + b^2 + 2 ceil4(m) b + b n + 2 b m + c b n)
  *   + 8 (3 b^2 + 2 G (l + 2) + 2 G (b + 1) + 4 b) + 4 (5 b + n) + 16
  * bytes, c = 0 (FP64) or 4 (FP32), ceil4(m) = m rounded up to a multiple of
  * 4: about 3.7 KB x n for FP64 at m = n, b = 64, p = 8 (n up to about 4400),
- * 2.9 KB x n for FP32 (n up to about 5700).  A problem needing more returns RQ_ETOOBIG before any
- * launch.  All calls share the array, so calls that overlap on the GPU race:
+ * 2.9 KB x n for FP32 (n up to about 5700).  A problem needing more returns
+ * RQ_ETOOBIG before any launch.  All calls share the array, so calls that overlap on the GPU race:
  * serialise them.  Each call looks up the array's address with the current
  * device; the first call on a device also loads the library there, so make
  * it before any stream capture.  prec is RQ_FP64 or RQ_FP32; argument errors
