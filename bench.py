@@ -565,7 +565,10 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True, f
     """4096 uneven problems in one persistent launch: the FP32 path (tile policy
     autotuned on the batch first, outside the timed region; every policy gives
     the same bits), the mixed mode beside it, and the plain FP64 path (rq_tuxv
-    in FP64, problem after problem: the batched kernel is FP32-only).
+    in FP64, problem after problem: the batched kernel is FP32-only).  A step
+    is one launch of the prepared batch (`problems_per_s`); `call_problems_per_s`
+    times the full Python call, whose per-problem marshalling is host-bound, and
+    `graph_problems_per_s` the launch captured in a CUDA graph.
 
     Quality, per sampled problem: each reduced-precision result's rank-k error
     over the FP64 path's on the same problem (the FP64 path matches the oracle
@@ -588,18 +591,31 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True, f
             tuning["tune_error"] = f"{type(exc).__name__}: {exc}"[:200]
 
     def timed(prec, outs):
-        outs, info = h.tuxv_batched(probs, prec=prec, outputs=outs)
-        for _ in range(warmup - 1):
-            h.tuxv_batched(probs, prec=prec, outputs=outs)
+        # the descriptors are built once (the batch's buffers stay the same);
+        # each step is one persistent launch
+        plan = h.prepare_batched(probs, outputs=outs)
+        for _ in range(warmup):
+            h.launch_prepared(plan, prec=prec)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            outs, info = h.launch_prepared(plan, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, outs, info
+
+    def timed_calls(prec, outs):
+        # the whole Python call per step: descriptors rebuilt and copied every time
         torch.cuda.synchronize()
         e0.record()
         for _ in range(steps):
             outs, info = h.tuxv_batched(probs, prec=prec, outputs=outs)
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps, outs, info
+        return e0.elapsed_time(e1) / steps
 
     ms, outs, info = timed(RQ_FP32, outs)
+    call_ms = timed_calls(RQ_FP32, outs)
     mms, mouts, minfo = timed(RQ_MIXED, None)
     # the same launch captured once in a CUDA graph and replayed (the call issues
     # one memset and one kernel, so the graph mainly removes host work)
@@ -632,6 +648,7 @@ def leg_batched(h, host, dev, steps=3, warmup=2, quality_sample=24, tune=True, f
            "problems_per_s": len(probs) / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
            "gbs_algorithmic": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / hbm_peak_gbs()[0],
            "info_nonzero": int((info != 0).sum()), **tuning, **graph,
+           "call_s": call_ms / 1e3, "call_problems_per_s": len(probs) / (call_ms / 1e3),
            "mixed": {"s": mms / 1e3, "problems_per_s": len(probs) / (mms / 1e3), "info_nonzero": int((minfo != 0).sum())}}
     g = np.random.default_rng(0)
     idx = g.choice(len(probs), size=min(quality_sample, len(probs)), replace=False)

@@ -77,6 +77,13 @@ def _used_on(t, stream):
     t.record_stream(stream)
 
 
+class _BatchPlan:
+    """Device descriptors and outputs of a batch prepared for repeated launches."""
+
+    def __init__(self, count, outputs, info, d, bounds):
+        self.count, self.outputs, self.info, self.d, self.bounds = count, outputs, info, d, bounds
+
+
 class Handle:
     """Owns one rq_handle (workspace cache) on the current CUDA device."""
 
@@ -185,6 +192,23 @@ class Handle:
         self._keep = d
         _used_on(d, stream)
         return outputs, info
+
+    def prepare_batched(self, problems, outputs=None, svd=False):
+        """Builds the device descriptors of a batch once (the per-problem Python
+        work of tuxv_batched: shapes, leading dimensions, pointers), for a batch
+        whose buffers are launched repeatedly (their contents may change between
+        launches).  Returns a plan for launch_prepared; plan.outputs and
+        plan.info hold the results of its latest launch."""
+        outputs, info, d, bounds = self._batch(problems, outputs, svd)
+        return _BatchPlan(len(problems), outputs, info, d, bounds)
+
+    def launch_prepared(self, plan, prec=RQ_MIXED, stream=None):
+        """One persistent launch of a prepared batch (rq_tuxv_batched on its
+        descriptors); returns (outputs, info)."""
+        rc = rq_tuxv_batched(self.h, prec, plan.count, plan.d, *plan.bounds, stream)
+        self._check(rc, "rq_tuxv_batched")
+        _used_on(plan.d, stream)
+        return plan.outputs, plan.info
 
     def tune_batched(self, problems, prec=RQ_MIXED, reps=2, passes=2, stream=None, outputs=None, svd=False,
                      cache=None, key=None):

@@ -186,3 +186,23 @@ def test_batched_graph_capture_and_replay(H):
     U, X, V = outs[0]
     assert torch.equal(U, ref[0][0]) and torch.equal(V, ref[0][2])
     assert torch.equal(X, 2.0 * ref[0][1])
+
+
+def test_prepared_batch_equals_the_call(H):
+    """A batch prepared once and launched twice gives the bits of tuxv_batched,
+    and its second launch (the buffers unchanged) the same bits again."""
+    import torch
+    from paper_2008_04447_gb300 import RQ_FP32
+    host = _mix(12, seed=8)
+    dev = _to_dev(host)
+    ref, info = H.tuxv_batched(dev, prec=RQ_FP32)
+    torch.cuda.synchronize()
+    ref = [tuple(t.clone() for t in o) for o in ref]
+    plan = H.prepare_batched(dev)
+    for _ in range(2):
+        outs, info2 = H.launch_prepared(plan, prec=RQ_FP32)
+        torch.cuda.synchronize()
+        assert int(info2.abs().sum()) == 0
+        for a, b in zip(ref, outs):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
