@@ -150,12 +150,14 @@ int rq_profile_read(rq_handle h, int nphases, double* ms, double* flops, double*
  *          (first such j; the factorisation still completes).
  * Precisions: RQ_FP64 and RQ_FP32 (RQ_MIXED returns RQ_ENOTIMPL: the BF16
  * sketch serves the truncated paths).  In FP64 the two block reflector
- * products of every block (W^T = (Y T)^T A2 and A2 -= Y W^T) run on the
- * bfloat16 tensor cores through the exact slice split of rq_gemm_f64, which
- * keeps FP64 accuracy; the handle's workspace then also holds the slices of
- * A2, about 16 m n bytes (the environment variable RQ_F64_TC, read when the
- * handle is created, selects "0": both products on the FP64 pipe, "1": only
- * the update on the tensor cores).  rq_qr and rq_rsrqrcp do the same.
+ * products of every block (W^T = (Y T)^T A2 and A2 -= Y W^T), the sketch
+ * B = Omega A and the sample update's product run on the bfloat16 tensor
+ * cores through the exact slice split of rq_gemm_f64, which keeps FP64
+ * accuracy; the handle's workspace then also holds the slices of A2, about
+ * 16 m n bytes (the environment variable RQ_F64_TC, read when the handle is
+ * created, selects "0": every product on the FP64 pipe, "1": only the update
+ * and the sample update on the tensor cores).  rq_qr and rq_rsrqrcp do the
+ * same.
  */
 int rq_rqrcp(rq_handle h, int prec, int m, int n, void* A, int lda, int b, int p, int k,
              const void* Omega, int ldo, void* tau, int* jpvt, int* info, rq_stream stream);
