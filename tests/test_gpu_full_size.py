@@ -59,6 +59,50 @@ def test_rqrcp_fp64_16384_invariants(H, graded16384):
     assert np.array_equal(jp[:upto], sq.perm[:upto])
 
 
+def _apply_qt(F, tau, X):
+    """Q^T X for the reflectors packed below the diagonal of F (v_i = 1 at row
+    i), applied one at a time in FP64 on the device: H_i X = X - tau_i v_i (v_i^T X)."""
+    import torch
+    X = X.clone()
+    m, k = F.shape[0], tau.shape[0]
+    for i in range(k):
+        v = F[i:, i].clone()
+        v[0] = 1.0
+        w = v @ X[i:]
+        X[i:] -= tau[i] * torch.outer(v, w)
+    return X
+
+
+def test_rqrcp_fp64_16384_sampled_residual(H, graded16384):
+    """The FP64 bar at the benchmark's size, on sampled columns: for columns j of
+    A P spread over the matrix, ||Q^T (A P) e_j - R e_j|| (= ||(A P - Q R) e_j||,
+    Q orthogonal), extrapolated over all n columns as sqrt(n mean(err_j^2)), is
+    at most 1e-12 ||A||_F; and Q^T keeps the Gram matrix of eight random vectors
+    to 1e-12 (the orthogonality of Q on a sampled subspace)."""
+    import torch
+    n, b, p = 16384, 64, 8
+    A0, Om = graded16384
+    A = torch.empty_like(A0)
+    A.copy_(A0)
+    tau, jpvt, info = H.rqrcp(A, Om, b, p)
+    torch.cuda.synchronize()
+    assert int(info.cpu()[0]) == 0
+    cols = torch.tensor([0, 1, 63, 64, 1000, 4095, 8191, 12000, 16000, 16383], device=A.device)
+    X = A0[:, jpvt.long()[cols]]
+    R = torch.triu(A)[:, cols]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(5)
+    Y = torch.randn(n, 8, generator=g, dtype=torch.float64).to(A.device)
+    Z = _apply_qt(A, tau, torch.cat([X, Y], dim=1))
+    err = torch.linalg.vector_norm(Z[:, :cols.numel()] - R, dim=0)
+    nrm = float(torch.linalg.norm(A0))
+    resid = float(torch.sqrt(n * torch.mean(err * err))) / nrm
+    assert resid <= 1e-12, resid
+    G0 = Y.T @ Y
+    G1 = Z[:, cols.numel():].T @ Z[:, cols.numel():]
+    assert float((G1 - G0).abs().max() / G0.abs().max()) <= 1e-12
+
+
 def test_rqrcp_fp32_16384_invariants(H, graded16384):
     """FP32 storage and 3xTF32 updates: the same invariants as the FP64 case
     with FP32 bounds -- column norms of R equal the pivoted columns' to 2e-4
