@@ -935,32 +935,58 @@ def main():
             tau_h = torch.empty(n, dtype=A0.dtype, pin_memory=True)
             jp_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
 
-            def e2e_step():
-                A.t().copy_(Ah, non_blocking=True)
+            from paper_2008_04447_gb300 import rq_copy
+            nbytes = A0.element_size() * m * n
+
+            def e2e_step(sm_copy):
+                # the 2.1 GB transfers by the library's SM copy (rq_copy) or the copy engines
+                if sm_copy:
+                    rc = rq_copy(A, Ah, nbytes, torch.cuda.current_stream().cuda_stream)
+                    if rc != 0:
+                        raise RuntimeError(f"rq_copy failed with status {rc}")
+                else:
+                    A.t().copy_(Ah, non_blocking=True)
                 tau, jpvt, info = h.rqrcp(A, Om, b, p)
-                Ao.copy_(A.t(), non_blocking=True)
+                if sm_copy:
+                    rc = rq_copy(Ao, A, nbytes, torch.cuda.current_stream().cuda_stream)
+                    if rc != 0:
+                        raise RuntimeError(f"rq_copy failed with status {rc}")
+                else:
+                    Ao.copy_(A.t(), non_blocking=True)
                 tau_h.copy_(tau, non_blocking=True)
                 jp_h.copy_(jpvt, non_blocking=True)
-            e2e_step()
-            torch.cuda.synchronize()
-            eclk = Clocks(local)
-            eclk.start()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            t0 = time.perf_counter()
-            ev0.record()
-            E = 2
-            for _ in range(E):
-                e2e_step()
-            ev1.record()
-            torch.cuda.synchronize()
-            e2e_s = (time.perf_counter() - t0) / E
-            e2e_dev_s = ev0.elapsed_time(ev1) / 1e3 / E
-            e2e_clocks = eclk.stop()
+
+            def e2e_run(sm_copy):
+                e2e_step(sm_copy)
+                torch.cuda.synchronize()
+                eclk = Clocks(local)
+                eclk.start()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                ev0.record()
+                E = 2
+                for _ in range(E):
+                    e2e_step(sm_copy)
+                ev1.record()
+                torch.cuda.synchronize()
+                return (time.perf_counter() - t0) / E, ev0.elapsed_time(ev1) / 1e3 / E, eclk.stop()
+
+            e2e_s, e2e_dev_s, e2e_clocks = e2e_run(True)
             esz = A0.element_size()
             line["e2e"] = {"value": fl / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
                            "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": e2e_s,
-                           "device_s_per_step": e2e_dev_s, "clocks": e2e_clocks}
+                           "device_s_per_step": e2e_dev_s, "clocks": e2e_clocks,
+                           "copies": "A in and R out by rq_copy (SM loads and stores through the pinned "
+                                     "buffers' device mapping); tau and jpvt by cudaMemcpyAsync"}
+            ce_s, ce_dev_s, _ = e2e_run(False)
+            line["e2e"]["copy_engine"] = {"value": fl / ce_s / 1e12, "s_per_step": ce_s,
+                                          "device_s_per_step": ce_dev_s}
+            Ah_check = Ao.clone()
+            e2e_step(True)
+            torch.cuda.synchronize()
+            line["e2e"]["sm_copy_matches_copy_engine"] = bool(torch.equal(Ao, Ah_check))
+            del Ah_check
             try:
                 line["e2e_pipelined"] = leg_e2e_pipelined(h, Ah, Ao, Om, b, p, fl, A, local)
             except Exception as exc:  # reported beside the serial number, never instead of it

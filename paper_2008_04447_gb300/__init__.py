@@ -16,7 +16,7 @@ from ._lib import (RQ_FP32, RQ_FP64, RQ_MIXED, RQ_OK, RQ_OP_QR, RQ_OP_RQRCP, RQ_
                    rq_gaussian, rq_profile_read, rq_qr, rq_rqrcp, rq_rsrqrcp, rq_set_workspace, rq_trqrcp,
                    rq_tuxv, rq_tuxv_batched, rq_tuxv_iter, rq_latent_cdf, rq_padding,
                    rq_workspace_size, rq_set_batch_tiles, rq_get_batch_tiles, rq_tiles_search, rq_tune_batched,
-                   rq_gemm_bf16, rq_gemm_f64, rq_selftest_wait_timeout)
+                   rq_gemm_bf16, rq_gemm_f64, rq_selftest_wait_timeout, rq_copy)
 
 __all__ = ["Handle", "colmajor", "RQ_FP64", "RQ_FP32", "RQ_MIXED"]
 

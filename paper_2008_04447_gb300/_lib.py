@@ -71,6 +71,7 @@ _SIGS = {
     "rq_padding": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], _I),
     "rq_gaussian": ([_P, _I, ctypes.c_uint64, ctypes.c_uint64, _I, _I, _P, _I, _P], _I),
     "rq_selftest_wait_timeout": ([_P, _P, _P], _I),
+    "rq_copy": ([_P, _P, ctypes.c_size_t, _P], _I),
 }
 
 # rq_problem: twelve int32 then seven 64-bit device pointers (104 bytes)
@@ -184,6 +185,20 @@ def rq_rqrcp(h, prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream
 def rq_rqrcp_noalloc(prec, m, n, A, lda, b, p, k, Omega, ldo, tau, jpvt, info, stream=None):
     return load().rq_rqrcp_noalloc(prec, m, n, _ptr(A), lda, b, p, k, _ptr(Omega), ldo, _ptr(tau), _ptr(jpvt),
                                    _ptr(info), _stream(stream))
+
+
+def _ptr_any(x):
+    """Address of a CUDA tensor, a pinned CPU tensor or a raw address."""
+    if x is None or isinstance(x, int):
+        return x
+    if not x.is_cuda and not x.is_pinned():
+        raise ValueError("CUDA or pinned CPU tensor expected")
+    return x.data_ptr()
+
+
+def rq_copy(dst, src, nbytes, stream=None):
+    """dst, src: raw addresses or tensors (CUDA, or pinned CPU)."""
+    return load().rq_copy(_ptr_any(dst), _ptr_any(src), nbytes, _stream(stream))
 
 
 def rq_selftest_wait_timeout(bar, info, stream=None):

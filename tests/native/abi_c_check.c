@@ -25,7 +25,7 @@ int main(void) {
       (fn_t)rq_latent_cdf,     (fn_t)rq_padding,       (fn_t)rq_qr,             (fn_t)rq_trqrcp,
       (fn_t)rq_tuxv,           (fn_t)rq_tuxv_iter,     (fn_t)rq_tuxv_batched,   (fn_t)rq_gemm_bf16,
       (fn_t)rq_set_batch_tiles, (fn_t)rq_get_batch_tiles, (fn_t)rq_tiles_search, (fn_t)rq_tune_batched,
-      (fn_t)rq_selftest_wait_timeout, (fn_t)rq_gemm_f64};
+      (fn_t)rq_selftest_wait_timeout, (fn_t)rq_gemm_f64, (fn_t)rq_copy};
   unsigned i, missing = 0;
   double prob = -1.0;
   int p = -1, rc, calls = 0;
