@@ -367,68 +367,6 @@ def leg_rsrqrcp(h, A0, A, Om, b, p, fl, rqrcp_ms, prec):
     return out
 
 
-def leg_e2e_pipelined(h, Ah, Ao_ref, Om, b, p, fl, like, local, steps=3):
-    """End to end with host buffers, pipelined across steps as a serving loop
-    would run it: two device copies of A alternate, and step i+1's input copy
-    and step i's result copy run on a copy stream while the factorisations run
-    on the compute stream.  Every step still moves its own input in and its own
-    result out inside the timed region.  Ordering: a buffer's input copy is
-    queued on the copy stream behind that buffer's previous result copy; a
-    factorisation waits for its input copy; a result copy waits for its
-    factorisation.  The last result is compared bit for bit with the serial
-    leg's (the FP64 path is deterministic)."""
-    import torch
-    n, m = Ah.shape
-    comp = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
-    bufs = [torch.empty_like(like), torch.empty_like(like)]
-    Ao = torch.empty(tuple(Ah.shape), dtype=Ah.dtype, pin_memory=True)
-    tau_h = torch.empty(n, dtype=Ah.dtype, pin_memory=True)
-    jp_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
-    done = [torch.cuda.Event(), torch.cuda.Event()]
-    keep = []                                   # step outputs stay alive until the end
-
-    def h2d(i):
-        with torch.cuda.stream(copy):
-            bufs[i % 2].t().copy_(Ah, non_blocking=True)
-            ready[i % 2].record(copy)
-
-    def step(i):
-        comp.wait_event(ready[i % 2])
-        tau, jpvt, info = h.rqrcp(bufs[i % 2], Om, b, p)
-        done[i % 2].record(comp)
-        keep.append((tau, jpvt, info))
-        if i + 1 < steps:
-            h2d(i + 1)
-        with torch.cuda.stream(copy):
-            copy.wait_event(done[i % 2])
-            Ao.copy_(bufs[i % 2].t(), non_blocking=True)
-            tau_h.copy_(tau, non_blocking=True)
-            jp_h.copy_(jpvt, non_blocking=True)
-
-    torch.cuda.synchronize()
-    clk = Clocks(local)
-    clk.start()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    start.record(copy)
-    h2d(0)
-    for i in range(steps):
-        step(i)
-    end.record(copy)
-    torch.cuda.synchronize()
-    wall = (time.perf_counter() - t0) / steps
-    dev = start.elapsed_time(end) / 1e3 / steps
-    esz = Ah.element_size()
-    out = {"value": fl / wall / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": esz * m * n,
-           "d2h_bytes_per_step": esz * m * n + (esz + 4) * n, "s_per_step": wall, "device_s_per_step": dev,
-           "steps": steps, "matches_serial": bool(torch.equal(Ao, Ao_ref)), "clocks": clk.stop(),
-           "overlap": "step i+1's input copy and step i's result copy beside the factorisations"}
-    del bufs, keep
-    return out
-
-
 def leg_slices(h):
     """Exactness of 8-bit slice products on the tensor cores: integer matrices
     with entries in [-255, 255] (the slices of an exact FP64 split) through
@@ -987,11 +925,6 @@ def main():
             torch.cuda.synchronize()
             line["e2e"]["sm_copy_matches_copy_engine"] = bool(torch.equal(Ao, Ah_check))
             del Ah_check
-            try:
-                line["e2e_pipelined"] = leg_e2e_pipelined(h, Ah, Ao, Om, b, p, fl, A, local)
-            except Exception as exc:  # reported beside the serial number, never instead of it
-                line["e2e_pipelined"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
-                torch.cuda.empty_cache()
             del Ah, Ao
         except Exception as exc:  # a failing extra leg must not lose the headline line
             line["e2e"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
