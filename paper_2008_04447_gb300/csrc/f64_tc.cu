@@ -486,20 +486,29 @@ cudaError_t oz_gemm(const Ctx& c, int M, int N, int K, const uint16_t* Ap, int M
   if (!make_plane_map(&ma, Ap, Kp, OZ_S * Mp, OZ_BM) || !make_plane_map(&mb, Bp, Kp, OZ_S * Np, OZ_BN))
     return cudaErrorInvalidValue;
   const int tiles = (Mp / OZ_BM) * (Np / OZ_BN);
-  // split K when the tiles do not fill the GPU (chunks of whole drains, partials in FP64)
+  // Split K (chunks of whole drains, partials in FP64) by the part count S that
+  // makes the launch shortest: the persistent CTAs run ceil(tiles S / SMs)
+  // waves of items of kchunk / 128 drains each, plus one drain's worth per item
+  // (pipeline fill and epilogue) and a small reduction per extra part.  Ties
+  // keep the smaller S.
   int S = 1;
-  if (c.splitk && K > 2 * kF64ChunkK && tiles < c.num_sms) {
-    S = (c.num_sms + tiles - 1) / tiles;
-    const int maxS = (K + kF64ChunkK - 1) / kF64ChunkK;
-    if (S > maxS) S = maxS;
-    const size_t cap = c.splitk_bytes / (sizeof(double) * (size_t)M * N);
-    if ((size_t)S > cap) S = (int)cap;
-    if (S < 2) S = 1;
-  }
   int kchunk = Kp;
-  if (S > 1) {
-    kchunk = ((K + S - 1) / S + kF64ChunkK - 1) / kF64ChunkK * kF64ChunkK;
-    S = (K + kchunk - 1) / kchunk;
+  const int nch = (K + kF64ChunkK - 1) / kF64ChunkK;
+  if (c.splitk && nch > 2) {
+    const size_t cap = c.splitk_bytes / (sizeof(double) * (size_t)M * N);
+    const int maxS = (size_t)nch < cap ? nch : (int)cap;
+    double best = (double)((tiles + c.num_sms - 1) / c.num_sms) * (nch + 1);
+    for (int s = 2; s <= maxS; ++s) {
+      const int kc = ((K + s - 1) / s + kF64ChunkK - 1) / kF64ChunkK * kF64ChunkK;
+      const int se = (K + kc - 1) / kc;
+      const long long waves = ((long long)tiles * se + c.num_sms - 1) / c.num_sms;
+      const double t = (double)waves * (kc / kF64ChunkK + 1) + 0.1 * se;
+      if (t < best) {
+        best = t;
+        S = se;
+        kchunk = kc;
+      }
+    }
   }
   OzArgs args;
   args.S = S;
