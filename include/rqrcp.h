@@ -381,11 +381,14 @@ int rq_gemm_bf16(rq_handle h, int M, int N, int K, const float* A, int lda, cons
  * the 36 slice pairs whose weights reach 2^-63 of the leading pair are
  * multiplied on the tensor cores, summed per weight in FP32 over at most 128
  * steps of K (exact: every partial sum stays below 2^24), gathered in int64
- * and returned to FP64 with one rounding.  The error is about that of an FP64
- * GEMM: below (3 K 2^-53 + 2^-52) 2^(ea_i + eb_j) per entry, with 2^ea_i and
- * 2^eb_j the powers of two just above the largest magnitude of row i of A and
- * column j of B (entries of 2^-1000 or less relative to their row's largest
- * lose accuracy to underflow).  The handle's workspace holds the slices:
+ * and returned to FP64 with one rounding (one per part when K is split over
+ * several CTAs, at most one part per 128 steps of K, whose FP64 partials are
+ * then summed).  The error is about that of an FP64 GEMM: below
+ * (3 K 2^-53 + 2^-52) 2^(ea_i + eb_j) per entry, with 2^ea_i and 2^eb_j the
+ * powers of two just above the largest magnitude of row i of A and column j
+ * of B, plus, for a result in the subnormal range, one unit 2^-1074 per part
+ * and one for their sum (entries of 2^-1000 or less relative to their row's
+ * largest lose accuracy to underflow).  The handle's workspace holds the slices:
  * 16 (ceil128(M) + ceil64(N)) ceil64(K) bytes, plus FP64 split-K partials.
  * Errors: -(argument index) for M, N or K < 1, a NULL array or a short
  * leading dimension (h is argument 1); RQ_ENOTIMPL without a tensor-map

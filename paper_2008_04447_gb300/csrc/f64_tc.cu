@@ -21,9 +21,12 @@
 // K ranges, for split-K) one after another.
 //   warp 0     : TMA producer: per 32-step K stage the eight A planes (128 x 32)
 //                and eight B planes (64 x 32), 96 KB, into a two-stage ring
-//   warp 1     : TMEM allocation and the single-thread tcgen05.mma issue, level
-//                by level; the first MMA of a chunk into level L waits until
-//                the drain warps have read level L of the previous chunk
+//   warp 1     : TMEM allocation and the single-thread tcgen05.mma issue: per
+//                16-step K slice one MMA per A plane i against B planes
+//                0..7-i at once (N up to 256; pair (i, j) lands in level i + j,
+//                so the B tiles and the TMEM columns are both contiguous), 12
+//                MMAs instead of 36; a chunk's first MMAs wait until the drain
+//                warps have read the levels they open
 //   warps 2..9 : drain TMEM level by level into int64 accumulators (warp w
 //                reads TMEM lane quarter w % 4, columns 32 ((w - 2) / 4) ..),
 //                and after a tile's last chunk the FP64 epilogue
@@ -70,9 +73,9 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t bf16_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = n (16 <= n <= 256, n % 16 == 0).
+__host__ __device__ constexpr uint32_t bf16_idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -192,7 +195,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = bf16_idesc();
       long long g = 0;   // stages consumed (all items)
       long long gc = 0;  // chunks issued (all items)
       bool ok = true;
@@ -204,23 +206,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           const int st = it % OZ_STAGES_PER_CHUNK;
           if (!mbar_wait(full(s), (uint32_t)((g / OZ_NS) & 1), a.err)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // A plane i times B planes 0..7-i in one MMA (N up to 256): the B plane
+          // tiles lie back to back in shared memory and pair (i, j) accumulates
+          // into level i + j, TMEM columns 64 (i + j) onward, so the output
+          // columns are contiguous too.
 #pragma unroll 1
-          for (int L = 0; L < OZ_S && ok; ++L) {
-            // the first stage of a chunk overwrites level L: the previous chunk's level L must be drained
-            if (st == 0 && gc > 0) {
-              if (!mbar_wait(ldrained(L), (uint32_t)((gc - 1) & 1), a.err)) { ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            }
-            const uint32_t d = tmem + (uint32_t)(L * OZ_BN);
+          for (int kk = 0; kk < OZ_BK / 16 && ok; ++kk) {
 #pragma unroll 1
-            for (int i = 0; i <= L; ++i) {
-              const uint32_t ai = smem_u32(sA(s, i));
-              const uint32_t bj = smem_u32(sB(s, L - i));
-#pragma unroll
-              for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-                // the pair (0, L) opens level L in each chunk
+            for (int i = 0; i < OZ_S && ok; ++i) {
+              const int ncols = (OZ_S - i) * OZ_BN;
+              for (int c0 = 0; c0 < ncols; c0 += 256) {
+                const int nn = ncols - c0 < 256 ? ncols - c0 : 256;
+                if (st == 0 && kk == 0 && i == 0 && gc > 0) {
+                  // this MMA opens levels c0/64 .. (c0+nn)/64-1: the previous chunk's must be drained
+                  for (int L = c0 / OZ_BN; L < (c0 + nn) / OZ_BN; ++L)
+                    if (!mbar_wait(ldrained(L), (uint32_t)((gc - 1) & 1), a.err)) { ok = false; break; }
+                  if (!ok) break;
+                  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                const uint32_t d = tmem + (uint32_t)(i * OZ_BN + c0);
+                const uint32_t ai = smem_u32(sA(s, i)) + kk * 32;
+                const uint32_t bj = smem_u32(sB(s, 0)) + (uint32_t)(c0 / OZ_BN) * OZ_BBYTES + kk * 32;
                 const uint32_t acc = (st == 0 && i == 0 && kk == 0) ? 0u : 1u;
-                mma_bf16(d, sw64_desc(ai + kk * 32), sw64_desc(bj + kk * 32), idesc, acc);
+                mma_bf16(d, sw64_desc(ai), sw64_desc(bj), bf16_idesc_n(nn), acc);
               }
             }
           }
@@ -429,6 +437,80 @@ __global__ void slice_rows_kernel(int R, int K, const double* __restrict__ src, 
   }
 }
 
+// The same for long K (K >= 512), where one thread per row leaves the GPU
+// nearly idle (Omega's 72 rows of the sketch): three passes over a 2-D grid.
+// (1) per-row largest f64_scale_exponent over the nonzero entries, by
+//     atomicMax into e preset to kNoExp (the function is monotone in |x|, so
+//     this equals the exponent of the row's largest magnitude);
+// (2) the planes from 32-row x 64-step tiles staged in shared memory, so that
+//     loads run along the rows and every plane store is a 128-byte row segment;
+// (3) kNoExp (an all-zero row) -> 0, the exponent of a zero row above.
+constexpr int kNoExp = -2139062144;  // 0x80808080, the byte 0x80 four times
+
+__global__ void __launch_bounds__(256) row_exp_max_kernel(int R, int K, const double* __restrict__ src, long long ld,
+                                                          int* __restrict__ e) {
+  __shared__ int s_ex[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  const int seg = blockIdx.y * 8 + w, nseg = gridDim.y * 8;
+  unsigned long long mx = 0;
+  if (r < R)
+    for (int k = seg; k < K; k += nseg) {
+      const unsigned long long b =
+          static_cast<unsigned long long>(__double_as_longlong(src[r + (long long)k * ld])) & 0x7fffffffffffffffull;
+      mx = b > mx ? b : mx;
+    }
+  s_ex[w][lane] = mx == 0 ? kNoExp : f64_scale_exponent(__longlong_as_double(static_cast<long long>(mx)));
+  __syncthreads();
+  if (w == 0 && r < R) {
+    int ex = s_ex[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) ex = s_ex[q][lane] > ex ? s_ex[q][lane] : ex;
+    if (ex != kNoExp) atomicMax(e + r, ex);
+  }
+}
+
+__global__ void __launch_bounds__(256) slice_rows_tiled_kernel(int R, int K, const double* __restrict__ src,
+                                                               long long ld, int Rp, int Kp,
+                                                               uint16_t* __restrict__ planes,
+                                                               const int* __restrict__ e) {
+  __shared__ double tile[64][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
+  // loads: warp w takes steps k0 + w + 8 i, lane = row
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int kk = w + 8 * i, k = k0 + kk, r = r0 + lane;
+    tile[kk][lane] = (r < R && k < K) ? src[r + (long long)k * ld] : 0.0;
+  }
+  __syncthreads();
+  // thread -> (row, eight consecutive steps); a warp writes four rows' 128-byte segments per plane
+  const int rr = threadIdx.x >> 3, oc = threadIdx.x & 7;
+  const int r = r0 + rr;
+  if (r >= Rp || k0 + 8 * oc >= Kp) return;
+  int ex = __ldg(e + r);
+  if (ex == kNoExp) ex = 0;
+  uint32_t wds[OZ_S][4];
+#pragma unroll
+  for (int t = 0; t < 8; t += 2) {
+    int s0[OZ_S], s1[OZ_S];
+    f64_slices(tile[8 * oc + t][rr], ex, s0);
+    f64_slices(tile[8 * oc + t + 1][rr], ex, s1);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) wds[i][t / 2] = bf16_bits_of(s0[i]) | (bf16_bits_of(s1[i]) << 16);
+  }
+  const size_t pstride = (size_t)Rp * Kp;
+  uint16_t* out = planes + (size_t)r * Kp + k0 + 8 * oc;
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+    *reinterpret_cast<uint4*>(out + i * pstride) = make_uint4(wds[i][0], wds[i][1], wds[i][2], wds[i][3]);
+}
+
+__global__ void no_exp_to_zero_kernel(int Rp, int* __restrict__ e) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < Rp && e[r] == kNoExp) e[r] = 0;
+}
+
 // C = alpha sum_z P_z + beta C over the split-K partials (P_z compact, M x N
 // column-major), C element (i, j) at C[i rs + j cs].
 __global__ void oz_reduce_kernel(int M, int N, int S, const double* __restrict__ P, size_t pzs, double alpha,
@@ -472,6 +554,16 @@ cudaError_t oz_slice(const Ctx& c, bool k_along_columns, int R, int K, const dou
     slice_cols_long_kernel<<<Rp, 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
   } else if (k_along_columns) {
     slice_cols_kernel<<<(Rp + 7) / 8, 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
+  } else if (K >= 512) {
+    cudaError_t em = cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)Rp, c.stream);
+    if (em != cudaSuccess) return em;
+    const int gx = (R + 31) / 32;
+    int gy = (K + 8 * 64 - 1) / (8 * 64);  // at least 64 steps per warp
+    if (gy > 64) gy = 64;
+    row_exp_max_kernel<<<dim3(gx, gy), 256, 0, c.stream>>>(R, K, src, ld, e);
+    slice_rows_tiled_kernel<<<dim3((Rp + 31) / 32, Kp / 64), 256, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
+    no_exp_to_zero_kernel<<<(Rp + 255) / 256, 256, 0, c.stream>>>(Rp, e);
+    *c.launches += 2;
   } else {
     slice_rows_kernel<<<(Rp + 127) / 128, 128, 0, c.stream>>>(R, K, src, ld, Rp, Kp, planes, e);
   }

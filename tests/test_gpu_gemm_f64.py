@@ -8,7 +8,10 @@ tests/test_f64_slices_host.py): |C - AB| <= (3 K 2^-53 + 2^-52) 2^(ea_i + eb_j)
 with 2^ea_i, 2^eb_j the powers of two just above the largest magnitude of
 row i of A and column j of B; and the Frobenius error within 10x that of an
 FP64 GEMM (numpy).  Shapes: ragged tiles, K = 1, one drain and many drains,
-split-K (few tiles, long K), graded and wide-range operands.
+split-K (few tiles, long K), graded and wide-range operands, and long K with
+zero, tiny, subnormal, huge and one-entry rows (the row slicer's 2-D path).
+A result in the subnormal range adds one unit 2^-1074 to the bound for each
+split-K part and one for their sum (each FP64 partial is rounded there).
 """
 import numpy as np
 import pytest
@@ -31,7 +34,7 @@ def _exp2_above(m):
 
 @pytest.mark.parametrize("M,N,K,kind", [(9, 5, 1, "gaussian"), (130, 70, 200, "gaussian"), (256, 64, 64, "graded"),
                                         (300, 257, 1000, "gaussian"), (64, 64, 4100, "gaussian"),
-                                        (200, 90, 333, "wide")])
+                                        (200, 90, 333, "wide"), (72, 40, 2000, "rows"), (70, 33, 700, "rows")])
 def test_gemm_f64_matches_the_extended_precision_product(H, M, N, K, kind):
     import torch
     from paper_2008_04447_gb300 import colmajor
@@ -43,6 +46,15 @@ def test_gemm_f64_matches_the_extended_precision_product(H, M, N, K, kind):
         B *= np.logspace(0, -8, K)[:, None]
     elif kind == "wide":
         A *= 10.0 ** g.uniform(-10, 10, (M, K))
+    elif kind == "rows":
+        # long K (the row slicer's 2-D path): an all-zero row, a row near the bottom of the
+        # normal range, a subnormal row, a huge row and a row with one nonzero entry
+        A[0] = 0.0
+        A[1] *= 1e-300
+        A[2] *= 5e-320
+        A[3] *= 1e300
+        A[4] = 0.0
+        A[4, K - 1] = 3.0
     C, info = H.gemm_f64(colmajor(torch.as_tensor(A)).cuda(), colmajor(torch.as_tensor(B)).cuda())
     torch.cuda.synchronize()
     assert int(info.cpu()[0]) == 0
@@ -51,7 +63,10 @@ def test_gemm_f64_matches_the_extended_precision_product(H, M, N, K, kind):
     err = np.abs(C.astype(np.longdouble) - ref).astype(np.float64)
     sa = _exp2_above(np.max(np.abs(A), axis=1))[:, None]
     sb = _exp2_above(np.max(np.abs(B), axis=0))[None, :]
-    bound = (3 * K * 2.0 ** -53 + 2.0 ** -52) * sa * sb
+    # plus subnormal units: a result below 2^-1022 is rounded to a multiple of 2^-1074 once per
+    # split-K part (at most one part per 128 steps of K) and once more by their sum
+    parts = -(-K // 128)
+    bound = (3 * K * 2.0 ** -53 + 2.0 ** -52) * sa * sb + (parts + 1) * 2.0 ** -1074
     assert np.all(err <= bound), float(np.max(err / bound))
     e_fp64 = float(np.linalg.norm((A @ B).astype(np.longdouble) - ref))
     e_tc = float(np.linalg.norm(err))
