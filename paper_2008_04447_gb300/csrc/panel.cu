@@ -254,7 +254,8 @@ struct FastArgs {
   TS* rowb;        // 2 * bj: row j of the panel
   unsigned int* bar;
   int* err;
-  int rpc;
+  int rpc;   // rows of CTAs 1.. (CTA c > 0 keeps rows [rpc0 + (c - 1) rpc, rpc0 + c rpc))
+  int rpc0;  // rows of CTA 0, which also forms T
 };
 
 // v[0..N) per lane, LPG lanes per group (N = 2 LPG): afterwards lane l of the
@@ -308,9 +309,13 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
   const int bj = a.bj;
   const int half = lane / LPG;
   const int lp = lane % LPG;
+  const int nrows = cta == 0 ? a.rpc0 : a.rpc;
+  const int rbase = cta == 0 ? 0 : a.rpc0 + (cta - 1) * a.rpc;
   const int r = warp * LPG + lp;
-  const int g = cta * a.rpc + r;
-  const bool live = r < a.rpc && g < a.mt;
+  const int g = rbase + r;
+  const bool live = r < nrows && g < a.mt;
+  // a warp with no row of the panel skips the per-row FP64 work (warp-uniform)
+  const bool wlive = warp * LPG < nrows && rbase + warp * LPG < a.mt;
   const int cbase = half * CPT;
   __shared__ TS s_tw[kFB];     // tau_j w_c, the lazy update's coefficients
   __shared__ TS s_sumT[kFB];   // global dot sums of this column
@@ -342,75 +347,81 @@ __global__ void __launch_bounds__(kThreads, 1) panel_fast_kernel(FastArgs<TS> a)
     TS* rowb = a.rowb + (size_t)par * bj;
     // (1) reflector j-1 on this row's columns >= j; pick up a_j(g)
     TS aj = TS(0);
-    const bool upd = j > 0 && live && g >= j - 1;
-    // finished columns (c < j) never change again: chunks of 16 columns that
-    // lie wholly below j are skipped
-#pragma unroll
-    for (int q0 = 0; q0 < CPT; q0 += 16) {
-      if (cbase + q0 + 16 > j) {
-#pragma unroll
-        for (int q = q0; q < q0 + 16; ++q) {
-          const int c = cbase + q;
-          if (upd && c >= j && c < bj) row[q] = fma(-s_tw[c], vprev, row[q]);
-          if (c == j) aj = row[q];
+    if (wlive) {
+      const bool upd = j > 0 && live && g >= j - 1;
+      // finished columns (c < j) never change again: chunks of 16 columns that
+      // lie wholly below j are skipped
+  #pragma unroll
+      for (int q0 = 0; q0 < CPT; q0 += 16) {
+        if (cbase + q0 + 16 > j) {
+  #pragma unroll
+          for (int q = q0; q < q0 + 16; ++q) {
+            const int c = cbase + q;
+            if (upd && c >= j && c < bj) row[q] = fma(-s_tw[c], vprev, row[q]);
+            if (c == j) aj = row[q];
+          }
         }
       }
-    }
-    if (TPR == 2) {
-      const TS o = __shfl_xor_sync(0xffffffffu, aj, 16);
-      if (half != j / CPT) aj = o;
-    }
-    if (live && g == j) {
-#pragma unroll
-      for (int q = 0; q < CPT; ++q)
-        if (cbase + q < bj) rowb[cbase + q] = row[q];
-    }
-    // (2) this row's share of the sums over rows g > j, reduced over the CTA;
-    // the squared norm in FP64 (float-float for FP32 rows)
-    const bool below = live && g > j;
-    const bool mine = below && half == j / CPT;
-    // (the products with finished columns, c < j, feed T's sums, which need
-    // every CTA's rows)
-    TS prod[CPT];
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-      const int c = cbase + q;
-      prod[q] = (below && c != j && c < bj) ? row[q] * aj : TS(0);
-    }
-    double x2d = 0.0;
-    if constexpr (kF32) {
-      // float-float squares while every |a_j(g)| of the warp lies in
-      // [2^-60, 2^55] (no overflow for up to 2^17 rows; about 2^-46 relative
-      // while the column's largest entries are at least 2^-52, falling toward
-      // 2^-34 for a column of entries near 2^-60, where the squares' low parts
-      // become subnormal); otherwise this warp sums in FP64
-      const float fa = fabsf(aj);
-      const bool out_of_range = mine && aj != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
-      if (__any_sync(0xffffffffu, out_of_range)) {
+      if (TPR == 2) {
+        const TS o = __shfl_xor_sync(0xffffffffu, aj, 16);
+        if (half != j / CPT) aj = o;
+      }
+      if (live && g == j) {
+  #pragma unroll
+        for (int q = 0; q < CPT; ++q)
+          if (cbase + q < bj) rowb[cbase + q] = row[q];
+      }
+      // (2) this row's share of the sums over rows g > j, reduced over the CTA;
+      // the squared norm in FP64 (float-float for FP32 rows)
+      const bool below = live && g > j;
+      const bool mine = below && half == j / CPT;
+      // (the products with finished columns, c < j, feed T's sums, which need
+      // every CTA's rows)
+      TS prod[CPT];
+  #pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        const int c = cbase + q;
+        prod[q] = (below && c != j && c < bj) ? row[q] * aj : TS(0);
+      }
+      double x2d = 0.0;
+      if constexpr (kF32) {
+        // float-float squares while every |a_j(g)| of the warp lies in
+        // [2^-60, 2^55] (no overflow for up to 2^17 rows; about 2^-46 relative
+        // while the column's largest entries are at least 2^-52, falling toward
+        // 2^-34 for a column of entries near 2^-60, where the squares' low parts
+        // become subnormal); otherwise this warp sums in FP64
+        const float fa = fabsf(aj);
+        const bool out_of_range = mine && aj != 0.f && (fa > 0x1p55f || fa < 0x1p-60f);
+        if (__any_sync(0xffffffffu, out_of_range)) {
+          x2d = mine ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
+          x2d = warp_sum(x2d);
+        } else {
+          float x2h = 0.f, x2l = 0.f;
+          if (mine) {
+            x2h = aj * aj;
+            x2l = fmaf(aj, aj, -x2h);
+          }
+  #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, x2h, o);
+            const float bl = __shfl_xor_sync(0xffffffffu, x2l, o);
+            ff_add(x2h, x2l, bh, bl);
+          }
+          if (lane == 0) x2d = static_cast<double>(x2h) + static_cast<double>(x2l);
+        }
+      } else {
         x2d = mine ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
         x2d = warp_sum(x2d);
-      } else {
-        float x2h = 0.f, x2l = 0.f;
-        if (mine) {
-          x2h = aj * aj;
-          x2l = fmaf(aj, aj, -x2h);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float bh = __shfl_xor_sync(0xffffffffu, x2h, o);
-          const float bl = __shfl_xor_sync(0xffffffffu, x2l, o);
-          ff_add(x2h, x2l, bh, bl);
-        }
-        if (lane == 0) x2d = static_cast<double>(x2h) + static_cast<double>(x2l);
       }
+      reduce_scatter<TS, CPT, LPG>(prod);
+      s_red[warp][cbase + 2 * lp] = prod[0];
+      s_red[warp][cbase + 2 * lp + 1] = prod[1];
+      if (lane == 0) s_redx[warp] = x2d;
     } else {
-      x2d = mine ? static_cast<double>(aj) * static_cast<double>(aj) : 0.0;
-      x2d = warp_sum(x2d);
+      s_red[warp][cbase + 2 * lp] = TS(0);
+      s_red[warp][cbase + 2 * lp + 1] = TS(0);
+      if (lane == 0) s_redx[warp] = 0.0;
     }
-    reduce_scatter<TS, CPT, LPG>(prod);
-    s_red[warp][cbase + 2 * lp] = prod[0];
-    s_red[warp][cbase + 2 * lp + 1] = prod[1];
-    if (lane == 0) s_redx[warp] = x2d;
     __syncthreads();
     if (tid < bj) {
       TS acc = TS(0);
@@ -547,7 +558,7 @@ cudaError_t panel_qr(const Ctx& c, TS* P, int ldp, int mt, int bj, TS* tau, TS* 
     constexpr int RPP = kThreads / TPR;
     // FP32 rows: as few CTAs as hold the panel (the step is latency-bound and
     // fewer CTAs make cheaper reductions); FP64 rows: the FP64 pipe bounds the
-    // step, so spread the rows over every SM (down to 64 rows per CTA)
+    // step, so spread the rows over every SM (below, in whole warps of rows)
     int Gf = (mt + RPP - 1) / RPP;
     if (sizeof(TS) == sizeof(double)) {
       const int g64 = (mt + 63) / 64;
@@ -560,12 +571,34 @@ cudaError_t panel_qr(const Ctx& c, TS* P, int ldp, int mt, int bj, TS* tau, TS* 
                                                                        kThreads, 0);
         if (eo != cudaSuccess) return eo;
       }
+      int rpc = (mt + Gf - 1) / Gf, rpc0 = rpc;
+      if (sizeof(TS) == sizeof(double)) {
+        // FP64 rows in whole warps (RPP / kWarps rows each): as few warps per CTA as the SMs
+        // allow (a warp without rows skips the per-row FP64 work), at least two, and CTA 0,
+        // which also forms T in FP64, one warp lighter when the grid still fits
+        const int wr = RPP / kWarps;
+        const int units = (mt + wr - 1) / wr;
+        const int gmax = c.num_sms < 4 * kMaxG4 ? c.num_sms : 4 * kMaxG4;
+        int k = (units + gmax - 1) / gmax;
+        if (k < 2) k = 2;
+        if (k > kWarps) k = kWarps;
+        int k0 = k - 1;
+        int g = units > k0 ? 1 + (units - k0 + k - 1) / k : 1;
+        if (g > gmax) {
+          k0 = k;
+          g = (units + k - 1) / k;
+        }
+        if (g <= gmax) {
+          Gf = g;
+          rpc = k * wr;
+          rpc0 = k0 * wr;
+        }
+      }
       if (per_sm_fast * c.num_sms >= Gf) {
-        const int rpc = (mt + Gf - 1) / Gf;
         TS* part = reinterpret_cast<TS*>(scratch);
         double* x2part = scratch + 2 * (size_t)Gf * bj;
         TS* rowb = reinterpret_cast<TS*>(x2part + 2 * (size_t)Gf);
-        FastArgs<TS> fa{P, ldp, mt, bj, tau, Y, ldy, T, ldt, part, x2part, rowb, c.bar, c.err, rpc};
+        FastArgs<TS> fa{P, ldp, mt, bj, tau, Y, ldy, T, ldt, part, x2part, rowb, c.bar, c.err, rpc, rpc0};
         void* fargs[] = {&fa};
         cudaError_t ef = cudaLaunchCooperativeKernel((const void*)panel_fast_kernel<TS, TPR>, dim3(Gf),
                                                      dim3(kThreads), fargs, 0, c.stream);
