@@ -147,34 +147,50 @@ __global__ void sample_update_idx_kernel(int bj, int n2, const double* __restric
 // rows at once, four threads per row (partial sums over i = sub mod 4, in a
 // fixed order), the rows kept in shared memory.
 template <typename TS>
-__global__ void omegahat_fast_kernel(const double* __restrict__ S11, int lds, const TS* __restrict__ R11, int ldr,
-                                     int bj, double* __restrict__ Oh, int ldo) {
-  extern __shared__ double so[];
-  double* sR = so;                   // bj x bj, column-major, upper
-  double* sX = sR + (size_t)bj * bj;  // sX[r + i * bj] = Oh(r, i)
-  double* sInv = sX + (size_t)bj * bj;
-  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) {
+// Oh = S11 R11^{-1} for b <= 64, right-looking: at step j the rows' entries of
+// column j are final (X(r, j) = W(r, j) / R(j, j)), and every later column of
+// the working copy W of S11 drops X(r, j) R(j, j') at once.  Each step is one
+// independent FP64 FMA per entry instead of a dependent dot product (an FP64
+// FMA waits about 64 cycles here), and the rows are split over CTAs of 16 rows
+// so that the FP64 work is spread over SMs.  Oh is upper triangular (S11 and
+// R11 are): rows r > j of column j are 0 and are skipped.
+__global__ void __launch_bounds__(256) omegahat_fast_kernel(const double* __restrict__ S11, int lds,
+                                                            const TS* __restrict__ R11, int ldr, int bj,
+                                                            double* __restrict__ Oh, int ldo) {
+  __shared__ double sR[64 * 64];   // sR[i * 64 + j] = R11(i, j), upper
+  __shared__ double sW[16 * 65];   // this CTA's rows of S11, then of Oh
+  __shared__ double sInv[64];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * 16;
+  for (int e = tid; e < bj * bj; e += 256) {
     const int i = e % bj, j = e / bj;
-    sR[e] = i <= j ? static_cast<double>(R11[i + (size_t)j * ldr]) : 0.0;
+    sR[i * 64 + j] = i <= j ? static_cast<double>(R11[i + (size_t)j * ldr]) : 0.0;
+  }
+  for (int e = tid; e < 16 * bj; e += 256) {
+    const int rr = e % 16, j = e / 16, r = r0 + rr;
+    sW[rr * 65 + j] = r < bj && r <= j ? S11[r + (size_t)j * lds] : 0.0;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < bj; j += blockDim.x) {
-    const double d = sR[j + (size_t)j * bj];
-    sInv[j] = d != 0.0 ? 1.0 / d : 0.0;
+  if (tid < bj) {
+    const double d = sR[tid * 64 + tid];
+    sInv[tid] = d != 0.0 ? 1.0 / d : 0.0;
   }
   __syncthreads();
-  const int r = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  const int rr = tid >> 4, cg = tid & 15, r = r0 + rr;
   for (int j = 0; j < bj; ++j) {
-    double acc = 0.0;
-    if (r < bj)
-      for (int i = r + sub; i < j; i += 4) acc = fma(sX[r + (size_t)i * bj], sR[i + (size_t)j * bj], acc);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (r < bj && sub == 0) sX[r + (size_t)j * bj] = j < r ? 0.0 : (S11[r + (size_t)j * lds] - acc) * sInv[j];
-    __syncwarp();
+    // X(r, j) for this CTA's rows r <= j (sixteen threads)
+    if (tid < 16 && r0 + tid < bj && r0 + tid <= j) sW[tid * 65 + j] *= sInv[j];
+    __syncthreads();
+    if (r < bj && r <= j) {
+      const double x = sW[rr * 65 + j];
+      for (int jj = j + 1 + cg; jj < bj; jj += 16) sW[rr * 65 + jj] = fma(-x, sR[j * 64 + jj], sW[rr * 65 + jj]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < bj * bj; e += blockDim.x) Oh[(e % bj) + (size_t)(e / bj) * ldo] = sX[e];
+  for (int e = tid; e < 16 * bj; e += 256) {
+    const int q = e % 16, j = e / 16, rw = r0 + q;
+    if (rw < bj) Oh[rw + (size_t)j * ldo] = sW[q * 65 + j];
+  }
 }
 
 // B1(:, t) -= Oh R12(:, t), R12(:, t) = Zb(:, idx[t]), for b <= 64: one CTA per
@@ -258,16 +274,7 @@ template <typename TS>
 cudaError_t omegahat11(const Ctx& c, const double* S11, int lds, const TS* R11, int ldr, int bj, double* Oh,
                        int ldo) {
   if (bj <= 64) {
-    const size_t smem = (2 * (size_t)bj * bj + bj) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t ea = cudaFuncSetAttribute(omegahat_fast_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)((2 * 64 * 64 + 64) * sizeof(double)));
-      if (ea != cudaSuccess) return ea;
-      attr = true;
-    }
-    const int threads = (4 * bj + 31) / 32 * 32;
-    omegahat_fast_kernel<TS><<<1, threads, smem, c.stream>>>(S11, lds, R11, ldr, bj, Oh, ldo);
+    omegahat_fast_kernel<TS><<<(bj + 15) / 16, 256, 0, c.stream>>>(S11, lds, R11, ldr, bj, Oh, ldo);
   } else {
     const int threads = bj <= 128 ? 128 : 256;
     omegahat_kernel<TS><<<(bj + threads - 1) / threads, threads, (size_t)bj * bj * sizeof(double), c.stream>>>(
