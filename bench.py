@@ -159,9 +159,9 @@ def bf16_peak_tflops():
 # DRAM bytes per trailing entry (m_t n2 of a block) moved by the two FP64
 # tensor-core products, from the ncu capture of a 6144 x 6144 factorisation
 # summarised in profiles/oz_gemm_fp64_6144_ncu.md: W = A2^T (Y T) reads A2's
-# slice planes once (1.03 x 16 B) and the update reads and writes A2
-# (0.91 x 16 B).  Valid while those kernels are unchanged.
-OZ_DRAM_BYTES_PER_ENTRY = 16.0 * (1.03 + 0.91)
+# slice planes once (1.035 x 16 B) and the update reads and writes A2
+# (0.905 x 16 B).  Valid while those kernels are unchanged.
+OZ_DRAM_BYTES_PER_ENTRY = 16.0 * (1.035 + 0.905)
 
 
 def trailing_entries(m, n, b, k=None):
