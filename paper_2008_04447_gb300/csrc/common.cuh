@@ -141,11 +141,12 @@ __device__ __forceinline__ void warp_argmax_key(long long& k, int& p, int& tag) 
 // x2 below it (Sec. 2): beta = -sign(alpha) ||a|| (sign(0) = +1), y1 = alpha -
 // beta, 1 / y1 and tau = (beta - alpha) / beta (= 2 / v^T v with v = y / y1),
 // from one division, 1 / (beta y1); tau = 2 exactly when x2 = 0 and all three
-// are 0 for a zero column.  With `fast` (data held in FP32) and
-// 2^-100 <= ||a||^2 < 2^100, the FP64 square root and reciprocal are one
-// Newton-Raphson step from the FP32 hardware results (Markstein's method:
-// each step doubles the correct bits, 24 -> about 47) instead of an FP64
-// square root and division, which cost about 650 cycles each on this part.
+// are 0 for a zero column.  For 2^-100 <= ||a||^2 < 2^100 the FP64 square
+// root and reciprocal are Newton-Raphson steps from the FP32 hardware results
+// (Markstein's method: each step doubles the correct bits) instead of an FP64
+// square root and division, which cost about 650 cycles each on this part:
+// one step with `fast` (data held in FP32: 24 -> about 47 bits), two for FP64
+// data (the second step's residual is exact by FMA: within about one ulp).
 __device__ __forceinline__ void householder_scalars(double alpha, double x2, bool fast, double& beta, double& inv,
                                                     double& tau) {
   const double nrm2 = fma(alpha, alpha, x2);
@@ -153,15 +154,18 @@ __device__ __forceinline__ void householder_scalars(double alpha, double x2, boo
   inv = 0.0;
   tau = 0.0;
   const int ex = static_cast<int>((__double_as_longlong(nrm2) >> 52) & 0x7ff);
-  if (fast && ex >= 1023 - 100 && ex < 1023 + 100) {
+  if (ex >= 1023 - 100 && ex < 1023 + 100) {
     const float s0f = sqrtf(static_cast<float>(nrm2));
     const double s0 = s0f;
-    const double nrm = fma(fma(-s0, s0, nrm2), static_cast<double>(0.5f / s0f), s0);
+    const double h = static_cast<double>(0.5f / s0f);
+    const double s1 = fma(fma(-s0, s0, nrm2), h, s0);
+    const double nrm = fast ? s1 : fma(fma(-s1, s1, nrm2), h, s1);
     beta = alpha >= 0.0 ? -nrm : nrm;
     const double y1 = alpha - beta;
     const double den = beta * y1;
     const double r0 = static_cast<double>(1.0f / static_cast<float>(den));
-    const double rr = fma(r0, fma(-den, r0, 1.0), r0);
+    const double r1 = fma(r0, fma(-den, r0, 1.0), r0);
+    const double rr = fast ? r1 : fma(r1, fma(-den, r1, 1.0), r1);
     inv = beta * rr;
     tau = x2 == 0.0 ? 2.0 : -y1 * (y1 * rr);
   } else if (nrm2 > 0.0) {

@@ -6,7 +6,8 @@ methods; the GPU parity tests cover the kernels that use them):
   and 1 / y1 formed from r = 1 / (beta y1) equal the paper's tau = 2 / v^T v
   (v = y / y1) and 1 / y1 to a few ulps;
 * FP64 square root and reciprocal by one Newton-Raphson step from the FP32
-  results (Markstein's method): at least 44 correct bits;
+  results (Markstein's method): at least 44 correct bits; by two steps (FP64
+  data, the second residual by a fused multiply-add): within 2^-52;
 * float-float (TwoSum) sums of squares of FP32 data, summed per thread and
   then by a 32-lane tree as the kernels do: relative error at most 2^-44 for
   entries of at least 2^-52 (measured about 2^-46 to 2^-48), checked against
@@ -14,6 +15,7 @@ methods; the GPU parity tests cover the kernels that use them):
   are subnormal, still within 2^-30.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -113,3 +115,32 @@ def test_float_float_sums_of_squares_are_fp64_accurate():
     x = (rng.standard_normal(32 * 8) * 2.0 ** -58).astype(np.float32)    # entries near 2^-58
     exact = math.fsum(float(a) * float(a) for a in x)
     assert abs(ff_thread_then_tree(x, 8) - exact) <= 2.0 ** -30 * exact
+
+
+def fma(a, b, c):
+    """a b + c rounded once (what the kernels' fma does)."""
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def newton2_sqrt(x):
+    s0 = float(np.sqrt(F32(x)))
+    h = float(F32(0.5) / F32(s0))
+    s1 = fma(fma(-s0, s0, x), h, s0)
+    return fma(fma(-s1, s1, x), h, s1)
+
+
+def newton2_rcp(d):
+    r0 = float(F32(1.0) / F32(d))
+    r1 = fma(r0, fma(-d, r0, 1.0), r0)
+    return fma(r1, fma(-d, r1, 1.0), r1)
+
+
+def test_two_newton_steps_give_fp64_square_roots_and_reciprocals():
+    rng = np.random.default_rng(2)
+    xs = np.exp2(rng.uniform(-100, 100, 4000)) * rng.uniform(1, 2, 4000)
+    for x in map(float, xs):
+        s = newton2_sqrt(x)
+        exact_s = Fraction(x)                      # compare s^2 with x exactly: |s - sqrt(x)| / sqrt(x) ~ |s^2 - x| / 2x
+        assert abs(Fraction(s) ** 2 - exact_s) / (2 * exact_s) <= Fraction(2) ** -52, x
+        r = newton2_rcp(x)
+        assert abs(Fraction(r) * Fraction(x) - 1) <= Fraction(2) ** -52, x
